@@ -1,0 +1,472 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks a property
+(orthogonality, permutation, conservation), a closed form (pulse speed,
+translated pulse, discrete identities), a library routine (FFT derivatives,
+numpy reductions) or an independent method (Yee FDTD) that a plausible mistake
+in the oracle (a dropped term, a wrong sign or index, a transposed operand)
+would break.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_13601_gb300 import media
+
+
+# ---------------------------------------------------------------------------
+# helpers (input generation and independent references)
+# ---------------------------------------------------------------------------
+
+def analytic_field(seed, ncomp, kmax=2):
+    """Random smooth periodic field on [0,1)^2 as an analytic sum of cosines."""
+    rng = np.random.default_rng(seed)
+    terms = []
+    for _ in range(ncomp):
+        tc = []
+        for kx in range(0, kmax + 1):
+            for ky in range(-kmax, kmax + 1):
+                if kx == 0 and ky <= 0:
+                    continue
+                tc.append((kx, ky, rng.normal() / (1 + kx * kx + ky * ky), rng.uniform(0, 2 * math.pi)))
+        terms.append(tc)
+
+    def ev(X, Y):
+        out = np.zeros((ncomp,) + np.shape(X))
+        for c in range(ncomp):
+            for kx, ky, a, ph in terms[c]:
+                out[c] += a * np.cos(2 * math.pi * (kx * X + ky * Y) + ph)
+        return out
+
+    return ev
+
+
+def spectral_d(f, axis, L=1.0):
+    N = f.shape[axis]
+    k = np.fft.fftfreq(N, d=L / N) * 2 * math.pi
+    shape = [1] * f.ndim
+    shape[axis] = N
+    return np.real(np.fft.ifft(1j * k.reshape(shape) * np.fft.fft(f, axis=axis), axis=axis))
+
+
+def eq16_rhs(q, nx, ny, nz, L=1.0):
+    """Right-hand side of Eq. 16 with spectral derivatives (x = axis 1, y = axis 0)."""
+    dx = lambda f: spectral_d(f, 1, L)
+    dy = lambda f: spectral_d(f, 0, L)
+    r = np.zeros_like(q)
+    r[0] = dy(q[5]) / nx
+    r[1] = -dx(q[5]) / ny
+    r[2] = (dx(q[4]) - dy(q[3])) / nz
+    r[3] = -dy(q[2] / nz)
+    r[4] = dx(q[2] / nz)
+    r[5] = -dx(q[1] / ny) + dy(q[0] / nx)
+    return r
+
+
+def local_matrix(apply, theta_vals):
+    """Extract the 6x6 matrix of a local operator: site x holds basis vector e_x."""
+    Nx, Ny = 6, 1
+    q = np.zeros((6, Ny, Nx))
+    for c in range(6):
+        q[c, 0, c] = 1.0
+    theta = np.empty((3, Ny, Nx))
+    for k in range(3):
+        theta[k] = theta_vals[k]
+    apply(q, theta)
+    return q[:, 0, :]  # column x = image of e_x
+
+
+# ---------------------------------------------------------------------------
+# Eq. 17 and Eq. 19: collision operators are orthogonal (unitary, real)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_collision_orthogonal(axis, seed):
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(-1.5, 1.5, size=3)
+    f = oracle.collide_x if axis == 0 else oracle.collide_y
+    M = local_matrix(lambda q, t: f(q, t, False), th)
+    Md = local_matrix(lambda q, t: f(q, t, True), th)
+    assert np.abs(M @ M.T - np.eye(6)).max() < 1e-15
+    assert abs(np.linalg.det(M) - 1.0) < 1e-14
+    np.testing.assert_allclose(Md, M.T, atol=1e-16)
+    # each collision mixes exactly two disjoint pairs and leaves two components alone
+    off = (np.abs(M - np.diag(np.diag(M))) > 0).sum()
+    assert off == 4
+
+
+def test_printed_cy_is_not_orthogonal():
+    """Eq. 19 as printed (sin theta2 of row 2 in column 4) is not orthogonal,
+    which is why the oracle reads that entry in column 3."""
+    t0, t2 = 0.3, 0.2
+    c0, s0, c2, s2 = math.cos(t0), math.sin(t0), math.cos(t2), math.sin(t2)
+    printed = np.array([
+        [c0, 0, 0, 0, 0, s0],
+        [0, 1, 0, 0, 0, 0],
+        [0, 0, c2, 0, s2, 0],
+        [0, 0, -s2, c2, 0, 0],
+        [0, 0, 0, 0, 1, 0],
+        [-s0, 0, 0, 0, 0, c0],
+    ])
+    assert np.abs(printed @ printed.T - np.eye(6)).max() > 0.1
+
+
+# ---------------------------------------------------------------------------
+# Streaming operators are permutations (bit-exact)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_streaming_is_permutation(axis):
+    rng = np.random.default_rng(3)
+    q0 = rng.standard_normal((6, 7, 9))
+    for comps in [(1, 4), (2, 5), (0, 3)]:
+        for d in (+1, -1):
+            q = q0.copy()
+            oracle.stream(q, comps[0], comps[1], axis, d)
+            ax = 2 if axis == 0 else 1
+            for c in range(6):
+                want = np.roll(q0[c], -d, axis=ax - 1) if c in comps else q0[c]
+                assert np.array_equal(q[c], want)
+            oracle.stream(q, comps[0], comps[1], axis, -d)
+            assert np.array_equal(q, q0)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_collide_stream_with_zero_angles_is_identity(axis):
+    """With theta = 0 every collision is I and the eight shifts of each
+    component cancel (Eq. 18, Eq. 20): U_X = U_Y = I exactly."""
+    rng = np.random.default_rng(4)
+    q0 = rng.standard_normal((6, 8, 10))
+    theta = np.zeros((3, 8, 10))
+    beta = np.zeros((4, 8, 10))
+    q = q0.copy()
+    oracle.collide_stream(q, theta, beta, axis, mid_v=True, vscale=0.5)
+    assert np.array_equal(q, q0)
+
+
+def test_zero_angle_step_is_identity():
+    """theta = beta = 0 (the delta -> 0 limit of Eq. 24-25): a full step is I."""
+    theta, beta = np.zeros((3, 10, 12)), np.zeros((4, 10, 12))
+    q0 = np.random.default_rng(5).standard_normal((6, 10, 12))
+    for seq in (oracle.SEQ_INTERLEAVED, oracle.SEQ_PLAIN):
+        for mode in (oracle.POT_PAPER, oracle.POT_UNITARY):
+            q = q0.copy()
+            oracle.step(q, theta, beta, seq, mode)
+            assert np.array_equal(q, q0)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 24 / Eq. 25: angles
+# ---------------------------------------------------------------------------
+
+def test_angles_closed_form():
+    N, delta, a = 64, 0.07, 0.3
+    x = np.arange(N)
+    prof = 1.4 + a * np.sin(2 * math.pi * x / N)
+    nx = np.tile(prof[:, None], (1, N))          # varies along y (axis 0)
+    ny = np.tile(prof[None, :], (N, 1))          # varies along x
+    nz = np.tile((prof + 0.2)[None, :], (N, 1))  # varies along x
+    theta, beta = oracle.angles(nx, ny, nz, delta)
+    np.testing.assert_allclose(theta[0], delta / (4 * nx), rtol=1e-15)
+    np.testing.assert_allclose(theta[1], delta / (4 * ny), rtol=1e-15)
+    np.testing.assert_allclose(theta[2], delta / (4 * nz), rtol=1e-15)
+    # central difference of a sinusoid: (f[i+1]-f[i-1])/2 = a sin(2 pi/N) cos(2 pi i/N)
+    dprof = a * math.sin(2 * math.pi / N) * np.cos(2 * math.pi * x / N)
+    np.testing.assert_allclose(beta[0], delta * dprof[None, :] / ny ** 2, atol=1e-15)
+    np.testing.assert_allclose(beta[1], delta * dprof[:, None] / nx ** 2, atol=1e-15)
+    np.testing.assert_allclose(beta[2], delta * dprof[None, :] / nz ** 2, atol=1e-15)
+    assert np.abs(beta[3]).max() == 0.0  # n_z does not vary along y
+
+
+# ---------------------------------------------------------------------------
+# Energy (Eq. 27) and div B definitions
+# ---------------------------------------------------------------------------
+
+def test_energy_is_mean_of_QdotQ():
+    q = np.random.default_rng(6).standard_normal((6, 13, 17))
+    assert abs(oracle.energy(q) - np.mean(np.sum(q * q, axis=0))) < 1e-14
+
+
+def test_divB_discrete_curl_is_divergence_free():
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((20, 24))
+    Dx = lambda f: 0.5 * (np.roll(f, -1, axis=1) - np.roll(f, 1, axis=1))
+    Dy = lambda f: 0.5 * (np.roll(f, -1, axis=0) - np.roll(f, 1, axis=0))
+    q = np.zeros((6, 20, 24))
+    q[3] = Dy(A)
+    q[4] = -Dx(A)
+    s, m, _ = oracle.divB(q)
+    assert m < 1e-14 and s < 1e-26
+
+
+def test_divB_closed_form():
+    Nx, Ny = 32, 6
+    x = np.arange(Nx)
+    q = np.zeros((6, Ny, Nx))
+    q[3] = np.sin(2 * math.pi * x / Nx)[None, :]
+    s, m, b = oracle.divB(q)
+    k = math.sin(2 * math.pi / Nx)
+    assert abs(s - Ny * (Nx / 2) * k * k) < 1e-12
+    assert abs(m - k) < 1e-14
+    assert abs(b - 1.0) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Pulse initialisation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_init_pulse_closed_form(pol):
+    Nx, Ny, x0, sig, A = 64, 3, 60.5, 5.0, -0.7
+    q = oracle.init_pulse(Nx, Ny, pol, x0, sig, A)
+    x = np.arange(Nx, dtype=float)
+    d = x - x0
+    d = d - Nx * np.round(d / Nx)
+    g = A * np.exp(-d * d / (2 * sig * sig))
+    if pol == 0:
+        np.testing.assert_allclose(q[2], np.tile(g, (Ny, 1)), atol=1e-15)
+        np.testing.assert_allclose(q[4], -np.tile(g, (Ny, 1)), atol=1e-15)
+        others = [0, 1, 3, 5]
+    else:
+        np.testing.assert_allclose(q[1], np.tile(g, (Ny, 1)), atol=1e-15)
+        np.testing.assert_allclose(q[5], np.tile(g, (Ny, 1)), atol=1e-15)
+        others = [0, 2, 3, 4]
+    assert all(np.abs(q[c]).max() == 0.0 for c in others)
+
+
+# ---------------------------------------------------------------------------
+# Conservation: unitary steps conserve the norm (Eq. 27 is the norm of Q)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seq", [oracle.SEQ_INTERLEAVED, oracle.SEQ_PLAIN])
+def test_energy_conserved_homogeneous(seq):
+    """Uniform anisotropic medium: all beta vanish, every operator is orthogonal."""
+    nx, ny, nz = media.uniform_medium(32, 32, (1.3, 1.7, 2.1))
+    theta, beta = oracle.angles(nx, ny, nz, 0.1)
+    assert np.abs(beta).max() == 0.0
+    q = media.smooth_periodic_field(32, 32, 5)
+    E0 = oracle.energy(q)
+    oracle.run(q, theta, beta, 1000, seq, oracle.POT_PAPER)
+    assert abs(oracle.energy(q) / E0 - 1) < 1e-12
+
+
+def test_energy_unitary_potential_inhomogeneous_and_paper_potential_not():
+    w = media.workload_cylinder_256()
+    nx, ny, nz = w.medium()
+    sl = (slice(64, 192), slice(0, 128))  # 128^2 window: cylinder edge plus pulse start
+    nx, ny, nz = (np.ascontiguousarray(a[sl]) for a in (nx, ny, nz))
+    theta, beta = oracle.angles(nx, ny, nz, 0.1)
+    q0 = oracle.init_pulse(128, 128, 0, 85.0, 8.0, 1.0)
+    E0 = oracle.energy(q0)
+    q = q0.copy()
+    oracle.run(q, theta, beta, 300, oracle.SEQ_INTERLEAVED, oracle.POT_UNITARY)
+    assert abs(oracle.energy(q) / E0 - 1) < 1e-12
+    q = q0.copy()
+    oracle.run(q, theta, beta, 300, oracle.SEQ_INTERLEAVED, oracle.POT_PAPER)
+    # the printed potentials are not unitary (Sec. 2.2): energy changes visibly
+    assert abs(oracle.energy(q) / E0 - 1) > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Polarisation families never couple (operator structure of Eq. 17-22)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("family", ["TE", "TM"])
+@pytest.mark.parametrize("mode", [oracle.POT_PAPER, oracle.POT_UNITARY])
+@pytest.mark.parametrize("seq", [oracle.SEQ_INTERLEAVED, oracle.SEQ_PLAIN])
+def test_te_tm_decoupled(family, mode, seq):
+    nx, ny, nz = media.smooth_periodic_medium(24, 20, seed=2, amp=0.3)
+    theta, beta = oracle.angles(nx, ny, nz, 0.2)
+    q = media.smooth_periodic_field(24, 20, 8)
+    te, tm = [0, 1, 5], [2, 3, 4]
+    zero = tm if family == "TE" else te
+    q[zero] = 0.0
+    oracle.run(q, theta, beta, 40, seq, mode)
+    assert all(np.abs(q[c]).max() == 0.0 for c in zero)
+    live = te if family == "TE" else tm
+    assert all(np.abs(q[c]).max() > 0.0 for c in live)
+
+
+# ---------------------------------------------------------------------------
+# Propagation: speed delta/n cells per step in +x (Eq. 24 with Delta t ~ delta^2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pol,nidx", [(0, 2), (1, 1)])
+def test_pulse_speed(pol, nidx):
+    Nx, Ny, d, steps = 1024, 1, 0.1, 1000
+    n = (1.2, 1.4, 1.6)
+    nx, ny, nz = media.uniform_medium(Nx, Ny, n)
+    theta, beta = oracle.angles(nx, ny, nz, d)
+    x0 = 300.0
+    for sigma, tol in ((20.0, 1.2e-3), (40.0, 5e-4)):
+        q = oracle.init_pulse(Nx, Ny, pol, x0, sigma, 1.0)
+        oracle.run(q, theta, beta, steps)
+        e = (q ** 2).sum(axis=0).mean(axis=0)
+        moved = (e * np.arange(Nx)).sum() / e.sum() - x0
+        expect = d * steps / n[nidx]  # uses n_z for E_z, n_y for E_y
+        assert abs(moved / expect - 1) < tol, (sigma, moved, expect)
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_second_order_convergence_to_exact_translation(pol):
+    """Uniform medium, fixed physical pulse: error vs the translated Gaussian
+    falls as delta^2 (Eq. 26 claims second order)."""
+    n = (1.3, 1.5, 1.7)
+    nn = n[2] if pol == 0 else n[1]
+    Lp, sig_p, T = 16.0, 1.0, 2.0
+    errs = []
+    for d in (0.2, 0.1, 0.05):
+        N = int(round(Lp / d))
+        nx, ny, nz = media.uniform_medium(N, 1, n)
+        theta, beta = oracle.angles(nx, ny, nz, d)
+        steps = int(round(T / d ** 2))
+        x0 = 5.0 / d
+        q = oracle.init_pulse(N, 1, pol, x0, sig_p / d, 1.0)
+        oracle.run(q, theta, beta, steps)
+        exact = oracle.init_pulse(N, 1, pol, x0 + (T / nn) / d, sig_p / d, 1.0)
+        errs.append(np.linalg.norm(q - exact) / np.linalg.norm(exact))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+# ---------------------------------------------------------------------------
+# Continuum limit in an inhomogeneous medium (Eq. 26 vs Eq. 16)
+# ---------------------------------------------------------------------------
+
+def _smooth_setup(N, seed_q=1, seed_n=2):
+    fq = analytic_field(seed_q, 6)
+    fn = analytic_field(seed_n, 3, kmax=1)
+    Y, X = np.meshgrid(np.arange(N) / N, np.arange(N) / N, indexing="ij")
+    q0 = fq(X, Y)
+    nf = fn(X, Y)
+    base = np.array([1.5, 1.3, 1.8])[:, None, None]
+    n = base * (1 + 0.15 * nf / np.abs(nf).max(axis=(1, 2), keepdims=True))
+    return q0, n
+
+
+@pytest.mark.parametrize("seq", [oracle.SEQ_INTERLEAVED, oracle.SEQ_PLAIN])
+def test_one_step_consistency_with_eq16(seq):
+    """(Q1 - Q0)/delta^2 -> RHS of Eq. 16 with the unitary potentials (second
+    order); the printed potentials leave a delta-independent residual."""
+    res = {oracle.POT_UNITARY: [], oracle.POT_PAPER: []}
+    for N in (32, 64, 128):
+        d = 1.0 / N
+        q0, n = _smooth_setup(N)
+        theta, beta = oracle.angles(n[0], n[1], n[2], d)
+        r = eq16_rhs(q0, n[0], n[1], n[2])
+        for mode in res:
+            q = q0.copy()
+            oracle.step(q, theta, beta, seq, mode)
+            res[mode].append(np.linalg.norm((q - q0) / d ** 2 - r) / np.linalg.norm(r))
+    u, p = res[oracle.POT_UNITARY], res[oracle.POT_PAPER]
+    assert u[-1] < 2e-3
+    assert all(1.9 < math.log2(u[i] / u[i + 1]) < 2.1 for i in range(2)), u
+    assert p[-1] > 0.02 and abs(p[-1] / p[-2] - 1) < 0.05, p
+
+
+class _Yee:
+    """Yee FDTD reference on an L x L periodic box for smooth analytic data."""
+
+    L = 4.0
+    T = 0.75
+
+    def __init__(self, N=512):
+        self.fq = analytic_field(11, 6, kmax=2)
+        self.fn = analytic_field(12, 3, kmax=1)
+        self.base = np.array([1.5, 1.3, 1.8])
+        h = self.L / N
+        nst = int(round(self.T / (0.25 * h)))
+        dt = self.T / nst
+        i = np.arange(N)
+        J, I = np.meshgrid(i, i, indexing="ij")
+        Xi, Yj, Xh, Yh = I * h, J * h, (I + 0.5) * h, (J + 0.5) * h
+        eps = np.zeros((3, N, N))
+        eps[0] = self.n(Xh, Yj)[0] ** 2
+        eps[1] = self.n(Xi, Yh)[1] ** 2
+        eps[2] = self.n(Xi, Yj)[2] ** 2
+        E = np.zeros((3, N, N))
+        B = np.zeros((3, N, N))
+        E[0] = self.f(Xh, Yj)[0] / self.n(Xh, Yj)[0]
+        E[1] = self.f(Xi, Yh)[1] / self.n(Xi, Yh)[1]
+        E[2] = self.f(Xi, Yj)[2] / self.n(Xi, Yj)[2]
+        B[0] = self.f(Xi, Yh)[3]
+        B[1] = self.f(Xh, Yj)[4]
+        B[2] = self.f(Xh, Yh)[5]
+        oracle.yee_run(eps, E, B, h, dt, nst)
+        self.N, self.E, self.B = N, E, B
+
+    def n(self, X, Y):
+        return self.base[:, None, None] * (1 + 0.1 * self.fn(X / self.L, Y / self.L))
+
+    def f(self, X, Y):
+        return self.fq(X / self.L, Y / self.L)
+
+    def as_q(self, Nq):
+        m = self.N // Nq
+        sl = lambda a: a[::m, ::m]
+        ax = lambda a: 0.5 * (a + np.roll(a, 1, axis=1))
+        ay = lambda a: 0.5 * (a + np.roll(a, 1, axis=0))
+        E, B = self.E, self.B
+        i = np.arange(Nq)
+        J, I = np.meshgrid(i, i, indexing="ij")
+        n = self.n(I * self.L / Nq, J * self.L / Nq)
+        return np.array([n[0] * sl(ax(E[0])), n[1] * sl(ay(E[1])), n[2] * sl(E[2]),
+                         sl(ay(B[0])), sl(ax(B[1])), sl(ay(ax(B[2])))])
+
+
+@pytest.fixture(scope="module")
+def yee_ref():
+    return _Yee(512)
+
+
+def test_yee_reference_plane_wave():
+    """The comparator itself: a vacuum plane wave E_z = cos(kx - wt), B_y = -cos(kx - wt)."""
+    N, L = 64, 1.0
+    h = L / N
+    dt = 0.2 * h
+    nst = 200
+    i = np.arange(N)
+    J, I = np.meshgrid(i, i, indexing="ij")
+    k = 2 * math.pi / L
+    eps = np.ones((3, N, N))
+    E = np.zeros((3, N, N))
+    B = np.zeros((3, N, N))
+    E[2] = np.cos(k * I * h)
+    B[1] = -np.cos(k * (I + 0.5) * h)
+    oracle.yee_run(eps, E, B, h, dt, nst)
+    t = nst * dt
+    # numerical dispersion of Yee is O((kh)^2): phase error k t (kh)^2/24 ~ 1e-3 here
+    np.testing.assert_allclose(E[2], np.cos(k * (I * h - t)), atol=5e-3)
+
+
+def test_yee_reference_self_convergence(yee_ref):
+    coarse = _Yee(256).as_q(128)
+    fine = yee_ref.as_q(128)
+    assert np.linalg.norm(coarse - fine) / np.linalg.norm(fine) < 3e-4
+
+
+def test_second_order_convergence_to_yee(yee_ref):
+    """Inhomogeneous anisotropic medium: QLA with the unitary potentials
+    converges to the brute-force Yee solve of the same curl equations at second
+    order; the printed potentials converge to something else."""
+    L, T = _Yee.L, _Yee.T
+    errs = {oracle.POT_UNITARY: [], oracle.POT_PAPER: []}
+    for N in (32, 64, 128):
+        d = L / N
+        i = np.arange(N)
+        J, I = np.meshgrid(i, i, indexing="ij")
+        n = yee_ref.n(I * d, J * d)
+        q0 = yee_ref.f(I * d, J * d)
+        theta, beta = oracle.angles(n[0], n[1], n[2], d)
+        steps = int(round(T / d ** 2))
+        ref = yee_ref.as_q(N)
+        for mode in errs:
+            q = q0.copy()
+            oracle.run(q, theta, beta, steps, oracle.SEQ_INTERLEAVED, mode)
+            errs[mode].append(np.linalg.norm(q - ref) / np.linalg.norm(ref))
+    u, p = errs[oracle.POT_UNITARY], errs[oracle.POT_PAPER]
+    assert all(1.8 < math.log2(u[i] / u[i + 1]) < 2.2 for i in range(2)), u
+    assert p[-1] > 5 * u[-1], (u, p)
