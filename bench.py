@@ -1,0 +1,302 @@
+"""Benchmark: QLA site-update throughput on the 8192^2 three-cylinder workload.
+
+A bench step = 100 QLA time steps (qla_step(100): fused passes of
+steps_per_pass steps) followed by one diagnostics reduction (energy Eq. 27,
+div B), i.e. one diagnostics interval of the workload. Inputs (the 1.6 GB FP32
+state) are far larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank runs its own replica of the workload (the
+lattices are independent: weak scaling, no data-path collective); value is the
+sum of site-updates over ranks divided by the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+window of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s per QLA step"
+UNIT = "site-updates/s"
+BYTES_PER_SITE_UPDATE = 60.0  # FP32 general kernel: 24 B state read + 24 B write + 12 B n_x, n_y, n_z
+QLA_STEPS_PER_BENCH_STEP = 100
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].strip() == "Active"})
+        pw = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(seconds: float = 12.0, impl_steps: int = 0):
+    """FP64 oracle on a bounded 1024^2 window of the workload (host cores)."""
+    import oracle
+    from paper_2301_13601_gb300 import media
+
+    w = media.workload_cylinders_8192()
+    N = 1024
+    # window around the pulse and the first cylinder edge, taken as its own periodic lattice
+    obj = min(w.objects, key=lambda o: o.cx)
+    y0 = int(max(0, min(w.Ny - N, obj.cy - N // 2)))
+    x0 = int(max(0, min(w.Nx - N, w.pulse.x0 - 256)))
+    objs =[media.Ellipse(o.cx - x0, o.cy - y0, o.a, o.b, o.angle, o.n, o.w) for o in w.objects]
+    nx, ny, nz = media.medium(N, N, objs)
+    theta, beta = oracle.angles(nx, ny, nz, w.delta)
+    q = oracle.init_pulse(N, N, w.pulse.pol, w.pulse.x0 - x0, w.pulse.sigma, w.pulse.amp)
+    steps = 0
+    t0 = time.perf_counter()
+    chunk = 5
+    while True:
+        oracle.run(q, theta, beta, chunk)
+        steps += chunk
+        el = time.perf_counter() - t0
+        if (impl_steps and steps >= impl_steps) or (not impl_steps and el >= seconds):
+            break
+    rate = N * N * steps / el
+    return {"value": rate, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, {N}x{N} window of the 8192^2 workload (pulse + cylinder), "
+                      f"{steps} QLA steps, {el:.1f} s"}, el, N * N * steps
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2301_13601_gb300 import media
+
+    w = media.workload_cylinders_8192()
+    N, S = 1024, 10
+    objs = [media.Ellipse(o.cx - 768, o.cy - 3584, o.a, o.b, o.angle, o.n, o.w) for o in w.objects]
+    nx, ny, nz = media.medium(N, N, objs)
+    theta, beta = oracle.angles(nx, ny, nz, w.delta)
+    q = oracle.init_pulse(N, N, w.pulse.pol, 256.0, w.pulse.sigma, w.pulse.amp)
+    for _ in range(args.warmup):
+        oracle.run(q, theta, beta, S)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(q, theta, beta, S)
+        oracle.energy(q)
+        oracle.divB(q)
+    el = time.perf_counter() - t0
+    value = N * N * S * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cylinders8192 (1024x1024 window)", "lattice": f"{N}x{N}", "delta": w.delta,
+                       "qla_steps_per_bench_step": S, "precision": "fp64", "sequence": "interleaved",
+                       "potential": "paper"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"{N}x{N} window, {S} QLA steps + diagnostics per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2301_13601_gb300 import build as _build
+    from paper_2301_13601_gb300 import media
+    from paper_2301_13601_gb300.qla import Simulation
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    _build.build()
+    w = media.workload_cylinders_8192()
+    n = w.medium()
+    S = QLA_STEPS_PER_BENCH_STEP
+    sim = Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass)
+    sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+    stream = sim.stream
+    sites = w.Nx * w.Ny
+
+    def bench_step():
+        sim.step(S)
+        return sim.diagnostics()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e_begin = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    sweep_ms = 0.0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    e_begin.record(stream)
+    last = None
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        sim.step(S)
+        ev[i][1].record(stream)
+        last = sim.diagnostics()
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    total_ms = e_begin.elapsed_time(e_end)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([total_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    total_ms = float(t.item())
+    site_updates = sites * S * args.steps * world
+    value = site_updates / (total_ms / 1e3)
+    launches_per_step = math.ceil(S / sim.steps_per_pass)
+    # e2e through the public API with host buffers: pinned H2D state copy,
+    # qla_step, diagnostics, D2H state copy, every bench step
+    host = torch.empty((6, w.Ny, w.Nx), dtype=torch.float32, pin_memory=True)
+    sim.get_fields_host_f32(host.data_ptr())
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_fields_host_f32(host.data_ptr())
+        sim.step(S)
+        sim.diagnostics()
+        sim.get_fields_host_f32(host.data_ptr())
+    e2e_s = time.perf_counter() - t0
+    e2e_value = sites * S * e2e_steps * world / e2e_s
+    sim.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    k = sim.steps_per_pass
+    launch_ms = sweep_ms / (args.steps * launches_per_step)
+    achieved = BYTES_PER_SITE_UPDATE * sites * k / (launch_ms / 1e3) / 1e9
+    cb, _, _ = cpu_baseline(seconds=args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cylinders8192_fp32", "lattice": f"{w.Nx}x{w.Ny}", "delta": w.delta,
+                   "qla_steps_per_bench_step": S, "steps_per_pass": k, "chunk_rows": sim.chunk_rows,
+                   "precision": "fp32", "sequence": "interleaved", "potential": "paper",
+                   "l2": "inputs larger than L2 (state 1.6 GB)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": f"sweep_kernel<float,{k}>", "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
+                     "note": "algorithmic bytes of the unfused step x steps fused per launch"},
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * sites * 4,
+                "d2h_bytes_per_step": 6 * sites * 4 + 40},
+        "clocks": clocks.summary(),
+        "gpu_launches": args.steps * (launches_per_step + 2),
+        "energy_last": last["energy"] if last else None,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--steps-per-pass", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * qla.h - C ABI of the GB300 qubit lattice algorithm (QLA) library, libqla.so.
+ *
+ * The library advances the 2D curl Maxwell equations in a diagonal-tensor
+ * dielectric with the QLA of arXiv 2301.13601 (Vahala et al.): at every site
+ * of a periodic Nx x Ny lattice the 6-qubit state
+ *     Q = (q0..q5) = (n_x E_x, n_y E_y, n_z E_z, B_x, B_y, B_z)        (Eq. 15)
+ * is advanced by collision rotations C_X, C_Y (Eq. 17, Eq. 19), one-cell
+ * streaming shifts (Eq. 18, Eq. 20) and the external potential operators V_X,
+ * V_Y (Eq. 21, Eq. 22), in the plain order of Eq. 23 or the interleaved order
+ * of Eq. 28, with collision angles from Eq. 24 and potential angles from Eq. 25.
+ *
+ * Conventions shared by every entry point:
+ *  - Host arrays are row-major [Ny][Nx] planes (x fastest); a state is 6 such
+ *    planes [6][Ny][Nx] in the component order of Eq. 15. Lattice units: sites
+ *    at integer (x, y), spacing delta in the physical units of Eq. 25.
+ *  - Streaming direction: S^{+x} sets q(x) <- q(x+1) and S^{-x} sets
+ *    q(x) <- q(x-1); operator products act right to left.
+ *  - Host buffers are owned by the caller and only read or written during the
+ *    call (copies are synchronous unless stated). Device buffers are owned by
+ *    the context unless the caller passes its own (qla_device_buffers).
+ *  - Every call returns a qla_status. QLA_EINVAL (bad argument) leaves the
+ *    context usable. Any CUDA failure is sticky: the context records the first
+ *    one, returns it from every later call and keeps its text for
+ *    qla_last_error() until qla_destroy().
+ *  - Calls on one context are not thread-safe; different contexts are
+ *    independent. Work runs on the context's stream, in call order.
+ */
+#ifndef QLA_H
+#define QLA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qla_ctx qla_ctx;
+
+typedef enum {
+    QLA_OK = 0,
+    QLA_EINVAL = 1,        /* invalid argument (sizes, delta, non-finite or non-positive n, NULL) */
+    QLA_ENOMEM = 2,        /* device or host allocation failed */
+    QLA_ECUDA = 3,         /* a CUDA runtime call failed (sticky) */
+    QLA_ETIMEOUT = 4,      /* a bounded device-side wait gave up (sticky) */
+    QLA_ENONFINITE = 5,    /* the state holds NaN or Inf (reported by the diagnostics) */
+    QLA_EUNSUPPORTED = 6,  /* option combination not built (e.g. unsupported steps_per_pass) */
+    QLA_ESTATE = 7         /* call out of order (e.g. step before any state was set) */
+} qla_status;
+
+enum { QLA_FP32 = 0, QLA_FP64 = 1 };                        /* state / arithmetic precision */
+enum { QLA_SEQ_INTERLEAVED = 0, QLA_SEQ_PLAIN = 1 };        /* Eq. 28 / Eq. 23 */
+enum { QLA_POT_PAPER = 0, QLA_POT_UNITARY = 1 };            /* V as printed / unitary variant */
+enum { QLA_POL_EZ = 0, QLA_POL_EY = 1 };                    /* pulse polarisation */
+
+/* Options for qla_create. Obtain defaults with qla_default_options().
+ * potential: QLA_POT_PAPER applies V_X, V_Y as printed (Eq. 21-22, with
+ *   row 3 of V_Y read as (0,0,sin b3,cos b3,0,0) and the "o" of its row 0 as
+ *   zero). QLA_POT_UNITARY rotates each coupled pair by half the angle instead,
+ *   so that every operator of the step is orthogonal (the fully unitary QLA
+ *   the paper's summary calls for). */
+typedef struct {
+    int precision;       /* QLA_FP32 (default) or QLA_FP64 (correctness mode) */
+    int sequence;        /* QLA_SEQ_INTERLEAVED (default, Eq. 28) or QLA_SEQ_PLAIN (Eq. 23) */
+    int potential;       /* QLA_POT_PAPER (default) or QLA_POT_UNITARY */
+    int steps_per_pass;  /* full time steps fused per HBM pass: 0 = automatic, else 1, 2 or 4 */
+    int chunk_rows;      /* rows of one sweep tile: 0 = automatic, else >= 8 */
+    int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
+    void *stream;        /* cudaStream_t to run on; NULL = a non-blocking stream owned by the context */
+} qla_options;
+
+/* Fill *opt with the defaults listed above. */
+void qla_default_options(qla_options *opt);
+
+/* Device memory one context needs (bytes; each buffer 256-byte aligned). */
+typedef struct {
+    size_t state_bytes;    /* one state buffer (6 planes); two are needed (ping-pong) */
+    size_t coeff_bytes;    /* rotation and potential coefficient planes */
+    size_t index_bytes;    /* n_x, n_y, n_z (double) */
+    size_t scratch_bytes;  /* reduction scratch for the diagnostics */
+} qla_buffer_sizes;
+
+/* Report the buffer sizes qla_create needs for an Nx x Ny lattice with these
+ * options (opt may be NULL for defaults). Errors: QLA_EINVAL for bad sizes. */
+qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_buffer_sizes *out);
+
+/* Caller-provided device buffers (each of the sizes above, on opt->device,
+ * 256-byte aligned). They must outlive the context; the context never frees
+ * them. */
+typedef struct {
+    void *state[2];
+    void *coeff;
+    void *index;
+    void *scratch;
+} qla_device_buffers;
+
+/* Create a context for an Nx x Ny periodic lattice (Nx, Ny >= 1, Nx*Ny <= 2^31).
+ * n_x, n_y, n_z: host [Ny][Nx] principal refractive indices (Eq. 15), copied.
+ * delta: the perturbation parameter (Eq. 24-25), 0 < delta <= 0.5.
+ * The collision angles theta_i = delta/(4 n_i) (Eq. 24) and potential angles
+ * beta from central differences of n (Eq. 25, lattice spacing delta) are
+ * computed once on the device in FP64 and stored as (cos-1, sin) pairs in the
+ * state precision; in FP32 each rotation pair is rounded so that
+ * (1 + m)^2 + s^2 is as close to 1 as FP32 allows.
+ * buffers: NULL = the library allocates with cudaMalloc and frees on destroy.
+ * The state is zero after creation. Errors: QLA_EINVAL (n <= 0, non-finite n or
+ * delta, bad sizes), QLA_ENOMEM, QLA_ECUDA. On error *out is NULL. */
+qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, const double *n_z,
+                      double delta, const qla_options *opt, const qla_device_buffers *buffers,
+                      qla_ctx **out);
+
+/* Set the state to a 1D Gaussian pulse travelling in +x, uniform in y
+ * (Sec. 2.2 and Sec. 4: a 1D pulse propagating in x):
+ *   g(x) = amplitude * exp(-d^2 / (2 sigma^2)),  d = periodic minimum-image x - x0,
+ *   QLA_POL_EZ: q2 = g, q4 = -g;  QLA_POL_EY: q1 = g, q5 = +g;  others 0.
+ * (the pairings follow the +x travelling solution of Eq. 16 in a uniform medium).
+ * Resets the step counter. Errors: QLA_EINVAL (sigma <= 0, bad polarisation). */
+qla_status qla_init_pulse(qla_ctx *ctx, int polarization, double x0, double sigma, double amplitude);
+
+/* Copy a host state [6][Ny][Nx] (double) into the context (rounded to the
+ * context precision). Resets the step counter. Synchronous. */
+qla_status qla_set_fields(qla_ctx *ctx, const double *q);
+
+/* Same with a float host state [6][Ny][Nx]; no rounding in FP32 mode.
+ * Asynchronous with respect to the host if q is pinned (page-locked) memory. */
+qla_status qla_set_fields_f32(qla_ctx *ctx, const float *q);
+
+/* Advance nsteps >= 0 time steps (Eq. 28 or Eq. 23). Asynchronous on the
+ * context stream; nsteps is split into fused passes of steps_per_pass steps
+ * plus shorter passes for the remainder. */
+qla_status qla_step(qla_ctx *ctx, long long nsteps);
+
+/* Energy (Eq. 27): the mean over sites of Q.Q, reduced in FP64 with
+ * compensated summation in a fixed order (deterministic). Synchronises the
+ * context stream. */
+qla_status qla_energy(qla_ctx *ctx, double *energy);
+
+/* div B with central differences in lattice units,
+ *   div = (B_x[x+1] - B_x[x-1])/2 + (B_y[y+1] - B_y[y-1])/2,  B = (q3, q4, q5),
+ * the diagnostic behind the paper's max div B/|B| < 1e-3 (Sec. 4.1):
+ * *l2_sq_sum = sum over sites of div^2, *max_abs = max |div|,
+ * *max_absB = max |B|. FP64, deterministic. Synchronises. */
+qla_status qla_divB(qla_ctx *ctx, double *l2_sq_sum, double *max_abs, double *max_absB);
+
+/* All diagnostics from one reduction pass. nonfinite = number of non-finite
+ * state values; when it is non-zero the call returns QLA_ENONFINITE (not
+ * sticky) with the other fields still filled in. */
+typedef struct {
+    double energy;       /* Eq. 27 */
+    double div_l2_sq;    /* sum div^2 */
+    double div_max;      /* max |div| */
+    double b_max;        /* max |B| */
+    long long nonfinite; /* NaN/Inf count */
+} qla_diag;
+
+qla_status qla_diagnostics(qla_ctx *ctx, qla_diag *out);
+
+/* Copy the state to a caller-owned host array [6][Ny][Nx] of double
+ * (or float). Synchronous. */
+qla_status qla_get_fields(qla_ctx *ctx, double *q);
+qla_status qla_get_fields_f32(qla_ctx *ctx, float *q);
+
+/* Device pointer to the current state (6 planes [6][Ny][Nx] of float or
+ * double, per the precision). Valid until the next qla_step. */
+void *qla_state_device_ptr(qla_ctx *ctx);
+
+/* Block the host until all queued work of the context has finished. */
+qla_status qla_synchronize(qla_ctx *ctx);
+
+/* Steps taken since the last state reset; -1 for a NULL context. */
+long long qla_step_count(const qla_ctx *ctx);
+
+/* Resolved configuration: steps per pass and rows per tile used by qla_step,
+ * and the precision. Any pointer may be NULL. */
+qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_rows, int *precision);
+
+/* Text of the last error on the context (empty string if none). */
+const char *qla_last_error(const qla_ctx *ctx);
+
+/* Name of a status code. */
+const char *qla_status_string(qla_status s);
+
+/* Release the context and any device memory it allocated. NULL is a no-op. */
+void qla_destroy(qla_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLA_H */

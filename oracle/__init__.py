@@ -17,6 +17,10 @@ import threading
 
 import numpy as np
 
+# Idle OpenMP threads sleep instead of spinning, so that the oracle does not
+# starve (or get starved by) other processes sharing the host cores.
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qla_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")

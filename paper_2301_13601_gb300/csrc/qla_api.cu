@@ -1,0 +1,463 @@
+// C ABI of libqla: context management, argument validation, buffer
+// ownership, pass scheduling and error reporting (declared in include/qla.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/qla.h"
+#include "qla_internal.h"
+
+struct qla_ctx {
+    int Nx = 0, Ny = 0;
+    double delta = 0.0;
+    qla_options opt{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool own_mem = false;
+    void *state[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *coef = nullptr;
+    double *index = nullptr;
+    void *scratch = nullptr;
+    qla::DiagResult *diag_dev = nullptr;
+    qla::DiagResult *diag_host = nullptr;
+    size_t esize = 4;
+    int K = 4;
+    int chunk = 0;
+    long long steps = 0;
+    bool has_state = false;
+    qla_status sticky = QLA_OK;
+    std::string msg;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+qla_status fail(qla_ctx *c, qla_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) {
+        if (s == QLA_ECUDA || s == QLA_ETIMEOUT) {
+            if (c->sticky == QLA_OK) {
+                c->sticky = s;
+                c->msg = buf;
+            }
+        } else {
+            c->msg = buf;
+        }
+    }
+    return s;
+}
+
+#define QLA_CUDA(ctx, expr)                                                                       \
+    do {                                                                                          \
+        cudaError_t _e = (expr);                                                                  \
+        if (_e != cudaSuccess)                                                                    \
+            return fail((ctx), QLA_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(_e));        \
+    } while (0)
+
+qla_status enter(qla_ctx *c) {
+    if (!c) return QLA_EINVAL;
+    if (c->sticky != QLA_OK) return c->sticky;
+    cudaError_t e = cudaSetDevice(c->dev);
+    if (e != cudaSuccess) return fail(c, QLA_ECUDA, "cudaSetDevice(%d): %s", c->dev, cudaGetErrorString(e));
+    return QLA_OK;
+}
+
+qla_status validate_sizes(int Nx, int Ny) {
+    if (Nx < 1 || Ny < 1) return QLA_EINVAL;
+    if ((long long)Nx * (long long)Ny > 2147483647LL) return QLA_EINVAL;
+    return QLA_OK;
+}
+
+void resolve_options(const qla_options *in, qla_options *out) {
+    qla_default_options(out);
+    if (in) *out = *in;
+}
+
+size_t elem_size(const qla_options &o) { return o.precision == QLA_FP64 ? 8 : 4; }
+
+int sm_count(int dev) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    return n;
+}
+
+// Rows per tile: choose the number of row chunks that minimises
+// (waves of CTAs) x (rows swept per CTA, warm-up included).
+int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
+    const int W = qla::sweep_strip_width();
+    const int wv = W - 8 * K;
+    const int nsx = (Nx + wv - 1) / wv;
+    const int occ = prec ? qla::sweep_occupancy_f64(K) : qla::sweep_occupancy_f32(K);
+    const long long slots = (long long)sms * occ;
+    double best = 1e300;
+    int best_chunk = Ny;
+    for (int ncy = 1; ncy <= std::max(1, Ny / 8); ++ncy) {
+        int ch = (Ny + ncy - 1) / ncy;
+        ch = (ch + 7) / 8 * 8;
+        if (ch > Ny) ch = Ny;
+        const int real_ncy = (Ny + ch - 1) / ch;
+        const long long ctas = (long long)nsx * real_ncy * 2;
+        const long long waves = (ctas + slots - 1) / slots;
+        const double cost = double(waves) * double(ch + 8 * K + 8 * (K - 1));
+        if (cost < best * 0.999) {
+            best = cost;
+            best_chunk = ch;
+        }
+        if (ctas > 64 * slots) break;
+    }
+    return std::max(1, best_chunk);
+}
+
+qla_status launch_pass(qla_ctx *c, int K) {
+    qla::SweepArgs a{};
+    a.q_in = c->state[c->cur];
+    a.q_out = c->state[c->cur ^ 1];
+    a.coef = c->coef;
+    a.Nx = c->Nx;
+    a.Ny = c->Ny;
+    a.w_valid = qla::sweep_strip_width() - 8 * K;
+    a.chunk = c->chunk;
+    a.interleaved = c->opt.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0;
+    a.unitary = c->opt.potential == QLA_POT_UNITARY ? 1 : 0;
+    a.vec = (c->Nx % int(16 / c->esize)) == 0 ? 1 : 0;
+    a.fam0 = 0;
+    cudaError_t e = c->opt.precision == QLA_FP64 ? qla::launch_sweep_f64(K, a, 2, c->stream)
+                                                  : qla::launch_sweep_f32(K, a, 2, c->stream);
+    if (e != cudaSuccess) return fail(c, QLA_ECUDA, "sweep launch (K=%d): %s", K, cudaGetErrorString(e));
+    c->cur ^= 1;
+    return QLA_OK;
+}
+
+qla_status run_diag(qla_ctx *c) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (!c->has_state) return fail(c, QLA_ESTATE, "no state set (call qla_init_pulse or qla_set_fields)");
+    cudaError_t e = qla::launch_diagnostics(c->state[c->cur], c->opt.precision == QLA_FP64 ? 1 : 0, c->Nx, c->Ny,
+                                            c->scratch, c->diag_dev, c->stream);
+    if (e != cudaSuccess) return fail(c, QLA_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
+    QLA_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_dev, sizeof(qla::DiagResult), cudaMemcpyDeviceToHost,
+                                c->stream));
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QLA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qla_default_options(qla_options *opt) {
+    if (!opt) return;
+    opt->precision = QLA_FP32;
+    opt->sequence = QLA_SEQ_INTERLEAVED;
+    opt->potential = QLA_POT_PAPER;
+    opt->steps_per_pass = 0;
+    opt->chunk_rows = 0;
+    opt->device = -1;
+    opt->stream = nullptr;
+}
+
+qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_buffer_sizes *out) {
+    if (!out || validate_sizes(Nx, Ny) != QLA_OK) return QLA_EINVAL;
+    qla_options o;
+    resolve_options(opt, &o);
+    if (o.precision != QLA_FP32 && o.precision != QLA_FP64) return QLA_EINVAL;
+    const size_t P = size_t(Nx) * size_t(Ny);
+    const size_t es = elem_size(o);
+    out->state_bytes = round_up(6 * P * es, kAlign);
+    out->coeff_bytes = round_up(size_t(qla::NCOEF) * P * es, kAlign);
+    out->index_bytes = round_up(3 * P * sizeof(double), kAlign);
+    out->scratch_bytes = round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign) + round_up(sizeof(qla::DiagResult), kAlign);
+    return QLA_OK;
+}
+
+qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, const double *n_z, double delta,
+                      const qla_options *opt, const qla_device_buffers *buffers, qla_ctx **out) {
+    if (!out) return QLA_EINVAL;
+    *out = nullptr;
+    if (validate_sizes(Nx, Ny) != QLA_OK || !n_x || !n_y || !n_z) return QLA_EINVAL;
+    if (!(delta > 0.0) || !(delta <= 0.5) || !std::isfinite(delta)) return QLA_EINVAL;
+    qla_options o;
+    resolve_options(opt, &o);
+    if (o.precision != QLA_FP32 && o.precision != QLA_FP64) return QLA_EINVAL;
+    if (o.sequence != QLA_SEQ_INTERLEAVED && o.sequence != QLA_SEQ_PLAIN) return QLA_EINVAL;
+    if (o.potential != QLA_POT_PAPER && o.potential != QLA_POT_UNITARY) return QLA_EINVAL;
+    if (o.steps_per_pass < 0 || o.chunk_rows < 0) return QLA_EINVAL;
+    if (o.steps_per_pass > 0 && !qla::sweep_supported(o.precision, o.steps_per_pass)) return QLA_EUNSUPPORTED;
+    const size_t P = size_t(Nx) * size_t(Ny);
+    const double *nn[3] = {n_x, n_y, n_z};
+    for (int k = 0; k < 3; ++k)
+        for (size_t i = 0; i < P; ++i)
+            if (!(nn[k][i] > 0.0) || !std::isfinite(nn[k][i])) return QLA_EINVAL;
+
+    qla_ctx *c = new qla_ctx();
+    c->Nx = Nx;
+    c->Ny = Ny;
+    c->delta = delta;
+    c->opt = o;
+    c->esize = elem_size(o);
+    auto bail = [&](qla_status s) {
+        qla_destroy(c);
+        return s;
+    };
+    if (o.device >= 0) {
+        if (cudaSetDevice(o.device) != cudaSuccess) return bail(QLA_ECUDA);
+        c->dev = o.device;
+    } else if (cudaGetDevice(&c->dev) != cudaSuccess) {
+        return bail(QLA_ECUDA);
+    }
+    if (cudaFree(nullptr) != cudaSuccess) return bail(QLA_ECUDA);  // context up
+    if (o.stream) {
+        c->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(QLA_ECUDA);
+        c->own_stream = true;
+    }
+    qla_buffer_sizes bs;
+    qla_query_buffer_sizes(Nx, Ny, &o, &bs);
+    if (buffers) {
+        if (!buffers->state[0] || !buffers->state[1] || !buffers->coeff || !buffers->index || !buffers->scratch)
+            return bail(QLA_EINVAL);
+        const void *ps[5] = {buffers->state[0], buffers->state[1], buffers->coeff, buffers->index, buffers->scratch};
+        for (const void *p : ps)
+            if ((reinterpret_cast<uintptr_t>(p) % kAlign) != 0) return bail(QLA_EINVAL);
+        c->state[0] = buffers->state[0];
+        c->state[1] = buffers->state[1];
+        c->coef = buffers->coeff;
+        c->index = static_cast<double *>(buffers->index);
+        c->scratch = buffers->scratch;
+    } else {
+        c->own_mem = true;
+        if (cudaMalloc(&c->state[0], bs.state_bytes) != cudaSuccess ||
+            cudaMalloc(&c->state[1], bs.state_bytes) != cudaSuccess ||
+            cudaMalloc(&c->coef, bs.coeff_bytes) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void **>(&c->index), bs.index_bytes) != cudaSuccess ||
+            cudaMalloc(&c->scratch, bs.scratch_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(QLA_ENOMEM);
+        }
+    }
+    c->diag_dev = reinterpret_cast<qla::DiagResult *>(static_cast<char *>(c->scratch) +
+                                                      round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign));
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->diag_host), sizeof(qla::DiagResult)) != cudaSuccess)
+        return bail(QLA_ENOMEM);
+    for (int k = 0; k < 3; ++k)
+        if (cudaMemcpyAsync(c->index + size_t(k) * P, nn[k], P * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess)
+            return bail(QLA_ECUDA);
+    if (qla::launch_coefficients(c->index, c->coef, Nx, Ny, delta, o.precision,
+                                 o.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0, o.potential == QLA_POT_UNITARY ? 1 : 0,
+                                 c->stream) != cudaSuccess)
+        return bail(QLA_ECUDA);
+    if (cudaMemsetAsync(c->state[0], 0, bs.state_bytes, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->state[1], 0, bs.state_bytes, c->stream) != cudaSuccess)
+        return bail(QLA_ECUDA);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(QLA_ECUDA);
+    c->K = o.steps_per_pass > 0 ? o.steps_per_pass : (o.precision == QLA_FP64 ? 2 : 4);
+    c->chunk = o.chunk_rows > 0 ? std::min(o.chunk_rows, Ny)
+                                : auto_chunk(Nx, Ny, c->K, o.precision == QLA_FP64 ? 1 : 0, sm_count(c->dev));
+    c->has_state = true;  // zero state
+    *out = c;
+    return QLA_OK;
+}
+
+qla_status qla_init_pulse(qla_ctx *c, int polarization, double x0, double sigma, double amplitude) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if ((polarization != QLA_POL_EZ && polarization != QLA_POL_EY) || !(sigma > 0.0) || !std::isfinite(x0) ||
+        !std::isfinite(sigma) || !std::isfinite(amplitude))
+        return fail(c, QLA_EINVAL, "qla_init_pulse: invalid argument");
+    cudaError_t e = qla::launch_init_pulse(c->state[c->cur], c->Nx, c->Ny, c->opt.precision == QLA_FP64 ? 1 : 0,
+                                           polarization, x0, sigma, amplitude, c->stream);
+    if (e != cudaSuccess) return fail(c, QLA_ECUDA, "pulse launch: %s", cudaGetErrorString(e));
+    c->steps = 0;
+    c->has_state = true;
+    return QLA_OK;
+}
+
+qla_status qla_set_fields(qla_ctx *c, const double *q) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (!q) return fail(c, QLA_EINVAL, "qla_set_fields: NULL");
+    const size_t n = 6 * size_t(c->Nx) * size_t(c->Ny);
+    if (c->opt.precision == QLA_FP64) {
+        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], q, n * 8, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<float> tmp(n);
+        for (size_t i = 0; i < n; ++i) tmp[i] = float(q[i]);
+        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], tmp.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = 0;
+    c->has_state = true;
+    return QLA_OK;
+}
+
+qla_status qla_set_fields_f32(qla_ctx *c, const float *q) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (!q) return fail(c, QLA_EINVAL, "qla_set_fields_f32: NULL");
+    const size_t n = 6 * size_t(c->Nx) * size_t(c->Ny);
+    if (c->opt.precision == QLA_FP32) {
+        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], q, n * 4, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<double> tmp(n);
+        for (size_t i = 0; i < n; ++i) tmp[i] = double(q[i]);
+        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], tmp.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    c->steps = 0;
+    c->has_state = true;
+    return QLA_OK;
+}
+
+qla_status qla_step(qla_ctx *c, long long nsteps) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (nsteps < 0) return fail(c, QLA_EINVAL, "qla_step: nsteps < 0");
+    if (!c->has_state) return fail(c, QLA_ESTATE, "qla_step: no state");
+    long long left = nsteps;
+    while (left > 0) {
+        int k = c->K;
+        while (k > 1 && (k > left || !qla::sweep_supported(c->opt.precision, k))) --k;
+        s = launch_pass(c, k);
+        if (s != QLA_OK) return s;
+        left -= k;
+        c->steps += k;
+    }
+    return QLA_OK;
+}
+
+qla_status qla_diagnostics(qla_ctx *c, qla_diag *out) {
+    if (!out) return fail(c, QLA_EINVAL, "qla_diagnostics: NULL");
+    qla_status s = run_diag(c);
+    if (s != QLA_OK) return s;
+    const qla::DiagResult &r = *c->diag_host;
+    out->energy = r.energy_sum / (double(c->Nx) * double(c->Ny));
+    out->div_l2_sq = r.div_sq_sum;
+    out->div_max = r.div_max;
+    out->b_max = r.b_max;
+    out->nonfinite = (long long)r.nonfinite;
+    if (r.nonfinite) return fail(c, QLA_ENONFINITE, "state holds %llu non-finite values", r.nonfinite);
+    return QLA_OK;
+}
+
+qla_status qla_energy(qla_ctx *c, double *energy) {
+    if (!energy) return fail(c, QLA_EINVAL, "qla_energy: NULL");
+    qla_diag d;
+    qla_status s = qla_diagnostics(c, &d);
+    if (s != QLA_OK && s != QLA_ENONFINITE) return s;
+    *energy = d.energy;
+    return s;
+}
+
+qla_status qla_divB(qla_ctx *c, double *l2_sq_sum, double *max_abs, double *max_absB) {
+    qla_diag d;
+    qla_status s = qla_diagnostics(c, &d);
+    if (s != QLA_OK && s != QLA_ENONFINITE) return s;
+    if (l2_sq_sum) *l2_sq_sum = d.div_l2_sq;
+    if (max_abs) *max_abs = d.div_max;
+    if (max_absB) *max_absB = d.b_max;
+    return s;
+}
+
+qla_status qla_get_fields(qla_ctx *c, double *q) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (!q) return fail(c, QLA_EINVAL, "qla_get_fields: NULL");
+    const size_t n = 6 * size_t(c->Nx) * size_t(c->Ny);
+    if (c->opt.precision == QLA_FP64) {
+        QLA_CUDA(c, cudaMemcpyAsync(q, c->state[c->cur], n * 8, cudaMemcpyDeviceToHost, c->stream));
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> tmp(n);
+        QLA_CUDA(c, cudaMemcpyAsync(tmp.data(), c->state[c->cur], n * 4, cudaMemcpyDeviceToHost, c->stream));
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < n; ++i) q[i] = double(tmp[i]);
+    }
+    return QLA_OK;
+}
+
+qla_status qla_get_fields_f32(qla_ctx *c, float *q) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (!q) return fail(c, QLA_EINVAL, "qla_get_fields_f32: NULL");
+    const size_t n = 6 * size_t(c->Nx) * size_t(c->Ny);
+    if (c->opt.precision == QLA_FP32) {
+        QLA_CUDA(c, cudaMemcpyAsync(q, c->state[c->cur], n * 4, cudaMemcpyDeviceToHost, c->stream));
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<double> tmp(n);
+        QLA_CUDA(c, cudaMemcpyAsync(tmp.data(), c->state[c->cur], n * 8, cudaMemcpyDeviceToHost, c->stream));
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < n; ++i) q[i] = float(tmp[i]);
+    }
+    return QLA_OK;
+}
+
+void *qla_state_device_ptr(qla_ctx *c) { return c ? c->state[c->cur] : nullptr; }
+
+qla_status qla_synchronize(qla_ctx *c) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QLA_OK;
+}
+
+long long qla_step_count(const qla_ctx *c) { return c ? c->steps : -1; }
+
+qla_status qla_get_config(const qla_ctx *c, int *steps_per_pass, int *chunk_rows, int *precision) {
+    if (!c) return QLA_EINVAL;
+    if (steps_per_pass) *steps_per_pass = c->K;
+    if (chunk_rows) *chunk_rows = c->chunk;
+    if (precision) *precision = c->opt.precision;
+    return QLA_OK;
+}
+
+const char *qla_last_error(const qla_ctx *c) { return c ? c->msg.c_str() : "NULL context"; }
+
+const char *qla_status_string(qla_status s) {
+    switch (s) {
+        case QLA_OK: return "QLA_OK";
+        case QLA_EINVAL: return "QLA_EINVAL";
+        case QLA_ENOMEM: return "QLA_ENOMEM";
+        case QLA_ECUDA: return "QLA_ECUDA";
+        case QLA_ETIMEOUT: return "QLA_ETIMEOUT";
+        case QLA_ENONFINITE: return "QLA_ENONFINITE";
+        case QLA_EUNSUPPORTED: return "QLA_EUNSUPPORTED";
+        case QLA_ESTATE: return "QLA_ESTATE";
+    }
+    return "unknown";
+}
+
+void qla_destroy(qla_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own_mem) {
+        cudaFree(c->state[0]);
+        cudaFree(c->state[1]);
+        cudaFree(c->coef);
+        cudaFree(c->index);
+        cudaFree(c->scratch);
+    }
+    if (c->diag_host) cudaFreeHost(c->diag_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+}  // extern "C"

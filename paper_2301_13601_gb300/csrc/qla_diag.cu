@@ -1,0 +1,163 @@
+// Diagnostics reduction: energy (Eq. 27), div B statistics and a non-finite
+// count in one pass over the state, reduced in FP64 with Neumaier-compensated
+// sums in a fixed order (the result depends only on the lattice size, not on
+// scheduling).
+//
+// Pass 1 (diag_partial): block b takes rows b, b + G, b + 2G, ...; every
+// thread keeps compensated sums over its sites; the block combines its
+// threads in a fixed tree and writes one partial record to scratch.
+// Pass 2 (diag_final): one block combines the G partials in a fixed tree.
+#include <math.h>
+
+#include "qla_internal.h"
+
+namespace qla {
+
+namespace {
+
+constexpr int DIAG_THREADS = 256;
+
+struct CSum {
+    double s, c;
+    __device__ __forceinline__ void add(double v) {
+        const double t = s + v;
+        if (fabs(s) >= fabs(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ void merge(const CSum &o) {
+        add(o.s);
+        c += o.c;
+    }
+};
+
+struct Partial {
+    double e_s, e_c, d_s, d_c, dmax, bmax;
+    unsigned long long nonfinite;
+    unsigned long long pad;
+};
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T v) {
+    return isfinite(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_partial(const T *__restrict__ q, int Nx, int Ny,
+                                                             Partial *__restrict__ part) {
+    const size_t P = size_t(Nx) * size_t(Ny);
+    const T *q3 = q + 3 * P, *q4 = q + 4 * P, *q5 = q + 5 * P;
+    CSum e{0.0, 0.0}, d{0.0, 0.0};
+    double dmax = 0.0, bmax = 0.0;
+    unsigned long long nf = 0;
+    for (int y = blockIdx.x; y < Ny; y += gridDim.x) {
+        const int yp = y + 1 == Ny ? 0 : y + 1, ym = y == 0 ? Ny - 1 : y - 1;
+        const size_t r = size_t(y) * Nx;
+        for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
+            const size_t i = r + x;
+            double site = 0.0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const T v = q[size_t(c) * P + i];
+                if (!finite_val(v)) ++nf;
+                const double dv = double(v);
+                site += dv * dv;
+            }
+            e.add(site);
+            const int xp = x + 1 == Nx ? 0 : x + 1, xm = x == 0 ? Nx - 1 : x - 1;
+            const double dv = 0.5 * (double(q3[r + xp]) - double(q3[r + xm])) +
+                              0.5 * (double(q4[size_t(yp) * Nx + x]) - double(q4[size_t(ym) * Nx + x]));
+            d.add(dv * dv);
+            dmax = fmax(dmax, fabs(dv));
+            const double b3 = double(q3[i]), b4 = double(q4[i]), b5 = double(q5[i]);
+            bmax = fmax(bmax, sqrt(b3 * b3 + b4 * b4 + b5 * b5));
+        }
+    }
+    __shared__ Partial sh[DIAG_THREADS];
+    sh[threadIdx.x] = Partial{e.s, e.c, d.s, d.c, dmax, bmax, nf, 0ull};
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            Partial a = sh[threadIdx.x];
+            const Partial b = sh[threadIdx.x + w];
+            CSum es{a.e_s, a.e_c}, ds{a.d_s, a.d_c};
+            es.merge(CSum{b.e_s, b.e_c});
+            ds.merge(CSum{b.d_s, b.d_c});
+            a.e_s = es.s; a.e_c = es.c; a.d_s = ds.s; a.d_c = ds.c;
+            a.dmax = fmax(a.dmax, b.dmax);
+            a.bmax = fmax(a.bmax, b.bmax);
+            a.nonfinite += b.nonfinite;
+            sh[threadIdx.x] = a;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS) diag_final(const Partial *__restrict__ part, int n,
+                                                           DiagResult *__restrict__ out) {
+    CSum e{0.0, 0.0}, d{0.0, 0.0};
+    double dmax = 0.0, bmax = 0.0;
+    unsigned long long nf = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Partial p = part[i];
+        e.merge(CSum{p.e_s, p.e_c});
+        d.merge(CSum{p.d_s, p.d_c});
+        dmax = fmax(dmax, p.dmax);
+        bmax = fmax(bmax, p.bmax);
+        nf += p.nonfinite;
+    }
+    __shared__ Partial sh[DIAG_THREADS];
+    sh[threadIdx.x] = Partial{e.s, e.c, d.s, d.c, dmax, bmax, nf, 0ull};
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            Partial a = sh[threadIdx.x];
+            const Partial b = sh[threadIdx.x + w];
+            CSum es{a.e_s, a.e_c}, ds{a.d_s, a.d_c};
+            es.merge(CSum{b.e_s, b.e_c});
+            ds.merge(CSum{b.d_s, b.d_c});
+            a.e_s = es.s; a.e_c = es.c; a.d_s = ds.s; a.d_c = ds.c;
+            a.dmax = fmax(a.dmax, b.dmax);
+            a.bmax = fmax(a.bmax, b.bmax);
+            a.nonfinite += b.nonfinite;
+            sh[threadIdx.x] = a;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const Partial a = sh[0];
+        out->energy_sum = a.e_s + a.e_c;
+        out->div_sq_sum = a.d_s + a.d_c;
+        out->div_max = a.dmax;
+        out->b_max = a.bmax;
+        out->nonfinite = a.nonfinite;
+    }
+}
+
+}  // namespace
+
+int diag_blocks(int Nx, int Ny) {
+    (void)Nx;
+    return Ny < 4 * 152 ? Ny : 4 * 152;
+}
+
+size_t diag_scratch_bytes(int Nx, int Ny) {
+    return size_t(diag_blocks(Nx, Ny)) * sizeof(Partial) + 256;
+}
+
+cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, void *scratch, DiagResult *out_dev,
+                               cudaStream_t st) {
+    const int G = diag_blocks(Nx, Ny);
+    Partial *part = static_cast<Partial *>(scratch);
+    if (precision == 0)
+        diag_partial<float><<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, part);
+    else
+        diag_partial<double><<<G, DIAG_THREADS, 0, st>>>(static_cast<const double *>(q), Nx, Ny, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final<<<1, DIAG_THREADS, 0, st>>>(part, G, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace qla

@@ -1,0 +1,93 @@
+// Internal declarations shared by the CUDA translation units of libqla.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qla {
+
+// Coefficient planes ([NCOEF][Ny][Nx], element type = state precision).
+// m = cos(angle) - 1, s = sin(angle) for the collision angles (Eq. 24);
+// vs = sin(b), vc = cos(b) - 1 for the effective potential angle b (Eq. 25,
+// scaled by 1/2 when interleaved (Eq. 28) and by 1/2 again for the unitary
+// potentials). Signs of the operators are applied by the kernels.
+enum CoefPlane {
+    C_TM_M = 0,   // theta_2 (x and y collisions of the TM family)
+    C_TM_S = 1,
+    C_TM_VXS = 2, // beta_2 (V_X row q4)
+    C_TM_VXC = 3,
+    C_TM_VYS = 4, // beta_3 (V_Y row q3)
+    C_TM_VYC = 5,
+    C_TE_XM = 6,  // theta_1 (C_X pair q1, q5)
+    C_TE_XS = 7,
+    C_TE_YM = 8,  // theta_0 (C_Y pair q0, q5)
+    C_TE_YS = 9,
+    C_TE_VXS = 10, // beta_0 (V_X row q5)
+    C_TE_VXC = 11,
+    C_TE_VYS = 12, // beta_1 (V_Y row q5)
+    C_TE_VYC = 13,
+    NCOEF = 14
+};
+
+// The six components split into two families that never couple (every
+// operator of Eq. 17-22 acts inside one of them):
+//   TM: hub q2, x-partner q4, y-partner q3   (E_z polarisation)
+//   TE: hub q5, x-partner q1, y-partner q0   (E_y polarisation)
+// In both families the first streaming group (S_14 along x, S_03 along y)
+// moves the partner and the second (S_25) moves the hub.
+struct Family {
+    int h, px, py;            // state planes
+    int cxm, cxs, cym, cys;   // collision coefficient planes
+    int vxs, vxc, vys, vyc;   // potential coefficient planes
+    float sgx, sgy;           // collision orientation: C acts as h += s h*m... see kernel
+    float tx, ty;             // potential orientation
+    int vx_hub, vy_hub;       // 1 if the potential row targets the hub, 0 if the partner
+};
+
+struct SweepArgs {
+    const void *q_in;   // [6][Ny][Nx]
+    void *q_out;        // [6][Ny][Nx]
+    const void *coef;   // [NCOEF][Ny][Nx]
+    int Nx, Ny;
+    int w_valid;        // output columns per strip
+    int chunk;          // output rows per tile
+    int interleaved;    // 1: Eq. 28, 0: Eq. 23
+    int unitary;        // 1: unitary potentials
+    int vec;            // 1: 16-byte vector access is legal (Nx multiple of 16/sizeof(T))
+    int fam0;           // first family index handled by blockIdx.z = 0 (0 = TM, 1 = TE)
+};
+
+// Sweep kernel launcher: one fused pass of K time steps over the lattice.
+// Returns cudaSuccess or the launch error.
+cudaError_t launch_sweep_f32(int K, const SweepArgs &a, int nfam, cudaStream_t st);
+cudaError_t launch_sweep_f64(int K, const SweepArgs &a, int nfam, cudaStream_t st);
+bool sweep_supported(int precision, int K);
+int sweep_strip_width();  // input columns per strip (halo included)
+int sweep_occupancy_f32(int K);  // resident CTAs per SM
+int sweep_occupancy_f64(int K);
+
+// Coefficients (Eq. 24-25) from the device index planes n[3][Ny][Nx] (double).
+cudaError_t launch_coefficients(const double *n, void *coef, int Nx, int Ny, double delta,
+                                int precision, int interleaved, int unitary, cudaStream_t st);
+// Pulse initial condition into state (precision-typed) [6][Ny][Nx].
+cudaError_t launch_init_pulse(void *q, int Nx, int Ny, int precision, int pol, double x0,
+                              double sigma, double amp, cudaStream_t st);
+// Conversions between a double/float staging buffer and the state.
+cudaError_t launch_convert(const void *src, int src_double, void *dst, int dst_double, size_t n,
+                           cudaStream_t st);
+
+// Diagnostics: partial reductions into scratch, then a single-block final pass.
+struct DiagResult {
+    double energy_sum;   // sum over sites of Q.Q
+    double div_sq_sum;
+    double div_max;
+    double b_max;
+    unsigned long long nonfinite;
+    unsigned long long pad[3];
+};
+int diag_blocks(int Nx, int Ny);
+size_t diag_scratch_bytes(int Nx, int Ny);
+cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, void *scratch,
+                               DiagResult *out_dev, cudaStream_t st);
+
+}  // namespace qla

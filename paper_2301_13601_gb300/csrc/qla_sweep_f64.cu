@@ -1,0 +1,22 @@
+// FP64 instantiations of the fused sweep (correctness mode; K = 1, 2).
+#include "qla_sweep.cuh"
+
+namespace qla {
+
+cudaError_t launch_sweep_f64(int K, const SweepArgs &a, int nfam, cudaStream_t st) {
+    switch (K) {
+        case 1: return launch_sweep_t<double, 1, 1, 4>(a, nfam, st);
+        case 2: return launch_sweep_t<double, 2, 2, 4>(a, nfam, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int sweep_occupancy_f64(int K) {
+    switch (K) {
+        case 1: return occupancy_t<double, 1, 1, 4>();
+        case 2: return occupancy_t<double, 2, 2, 4>();
+        default: return 1;
+    }
+}
+
+}  // namespace qla

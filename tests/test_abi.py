@@ -1,0 +1,80 @@
+"""The C-ABI library loads on any machine and exports every symbol include/qla.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "qla.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qla_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2301_13601_gb300 import qla
+
+    return ctypes.CDLL(qla.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("qla_create", "qla_init_pulse", "qla_step", "qla_energy", "qla_divB", "qla_get_fields",
+                     "qla_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2301_13601_gb300 import qla
+
+    assert sorted(qla.EXPORTS) == declared_functions()
+
+
+def test_status_strings_without_gpu(lib):
+    lib.qla_status_string.restype = ctypes.c_char_p
+    assert lib.qla_status_string(0) == b"QLA_OK"
+    assert lib.qla_status_string(4) == b"QLA_ETIMEOUT"
+
+
+def test_buffer_size_query_without_gpu(lib):
+    from paper_2301_13601_gb300 import qla
+
+    L = qla.load_library()
+    sizes = qla.BufferSizes()
+    assert L.qla_query_buffer_sizes(100, 50, None, ctypes.byref(sizes)) == 0
+    assert sizes.state_bytes >= 6 * 100 * 50 * 4 and sizes.state_bytes % 256 == 0
+    assert sizes.coeff_bytes >= 14 * 100 * 50 * 4
+    assert L.qla_query_buffer_sizes(0, 50, None, ctypes.byref(sizes)) == 1
+    assert L.qla_query_buffer_sizes(70000, 70000, None, ctypes.byref(sizes)) == 1
+
+
+def test_create_rejects_bad_arguments_before_touching_a_gpu(lib):
+    import numpy as np
+
+    from paper_2301_13601_gb300 import qla
+
+    L = qla.load_library()
+    n = np.ones((4, 4))
+    bad = n.copy()
+    bad[1, 2] = -1.0
+    ctx = ctypes.c_void_p()
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.qla_create(4, 4, P(n), P(n), P(bad), 0.1, None, None, ctypes.byref(ctx)) == 1
+    nan = n.copy()
+    nan[0, 0] = np.nan
+    assert L.qla_create(4, 4, P(nan), P(n), P(n), 0.1, None, None, ctypes.byref(ctx)) == 1
+    assert L.qla_create(4, 4, P(n), P(n), P(n), 0.0, None, None, ctypes.byref(ctx)) == 1
+    assert L.qla_create(4, 4, P(n), P(n), P(n), 0.7, None, None, ctypes.byref(ctx)) == 1
+    assert not ctx.value

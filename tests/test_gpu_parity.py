@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  FP64 mode: relative L2 <= 1e-12 (the GPU evaluates the same rotations in a
+             different rounding order: ~1e-16 per operation).
+  FP32 mode: per step ~64 roundings of relative size 2^-24 per component, so
+             the relative L2 error grows like sqrt(steps) * 1e-7 to 1e-6;
+             bounds below are stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_13601_gb300 import media
+from paper_2301_13601_gb300.qla import QLAError, Simulation
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_run(n, q0, delta, steps, **kw):
+    with Simulation(*n, delta, **kw) as sim:
+        sim.set_fields(q0)
+        sim.step(steps)
+        return sim.get_fields()
+
+
+def oracle_run(n, q0, delta, steps, sequence="interleaved", potential="paper"):
+    theta, beta = oracle.angles(*n, delta)
+    q = np.array(q0, dtype=np.float64, copy=True)
+    oracle.run(q, theta, beta, steps, oracle.SEQ_INTERLEAVED if sequence == "interleaved" else oracle.SEQ_PLAIN,
+               oracle.POT_PAPER if potential == "paper" else oracle.POT_UNITARY)
+    return q
+
+
+# lattice shapes: several strips with a ragged tail and several row chunks,
+# odd sizes (scalar-load path), a tiny lattice narrower than a strip
+SHAPES = [(500, 70, 24), (37, 53, 0), (8, 5, 0), (64, 64, 16)]
+
+
+def problem(Nx, Ny, seed=3):
+    n = media.smooth_periodic_medium(Nx, Ny, seed=seed, amp=0.3)
+    q0 = media.smooth_periodic_field(Nx, Ny, seed + 10)
+    # add small-scale structure so that every shift matters
+    q0 += 0.1 * np.random.default_rng(seed).standard_normal(q0.shape)
+    return n, q0
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("K", [1, 2])
+@pytest.mark.parametrize("sequence", ["interleaved", "plain"])
+@pytest.mark.parametrize("potential", ["paper", "unitary"])
+def test_fp64_matches_oracle(shape, K, sequence, potential):
+    Nx, Ny, chunk = shape
+    n, q0 = problem(Nx, Ny)
+    delta, steps = 0.2, 2 * K + 1
+    got = gpu_run(n, q0, delta, steps, precision="fp64", steps_per_pass=K, chunk_rows=chunk,
+                  sequence=sequence, potential=potential)
+    ref = oracle_run(n, q0, delta, steps, sequence, potential)
+    assert rel_l2(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("K", [1, 2, 4])
+@pytest.mark.parametrize("sequence", ["interleaved", "plain"])
+@pytest.mark.parametrize("potential", ["paper", "unitary"])
+def test_fp32_matches_oracle(shape, K, sequence, potential):
+    Nx, Ny, chunk = shape
+    n, q0 = problem(Nx, Ny)
+    delta, steps = 0.2, 3 * K + 1
+    got = gpu_run(n, q0, delta, steps, precision="fp32", steps_per_pass=K, chunk_rows=chunk,
+                  sequence=sequence, potential=potential)
+    ref = oracle_run(n, q0, delta, steps, sequence, potential)
+    assert rel_l2(got, ref) < 3e-6
+
+
+def test_pulse_init_matches_oracle():
+    for pol, name in ((0, "Ez"), (1, "Ey")):
+        Nx, Ny = 300, 20
+        n = media.uniform_medium(Nx, Ny, (1.0, 1.0, 1.0))
+        with Simulation(*n, 0.1, precision="fp64") as sim:
+            sim.init_pulse(name, 250.5, 30.0, -0.8)
+            got = sim.get_fields()
+        ref = oracle.init_pulse(Nx, Ny, pol, 250.5, 30.0, -0.8)
+        assert np.abs(got - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cylinder_256_full_run(precision):
+    """256^2, delta 0.1, 400 steps, cylinder R 30, E_z pulse: the full workload."""
+    w = media.workload_cylinder_256()
+    n = w.medium()
+    theta, beta = oracle.angles(*n, w.delta)
+    ref = oracle.init_pulse(w.Nx, w.Ny, w.pulse.pol, w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+    oracle.run(ref, theta, beta, w.steps)
+    with Simulation(*n, w.delta, precision=precision) as sim:
+        sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+        sim.step(w.steps)
+        got = sim.get_fields()
+        e = sim.energy()
+        dv = sim.divB()
+    E0 = oracle.energy(oracle.init_pulse(w.Nx, w.Ny, 0, w.pulse.x0, w.pulse.sigma, w.pulse.amp))
+    if precision == "fp64":
+        assert rel_l2(got, ref) < 1e-12
+        # energy is quadratic in the fields: twice the field tolerance
+        assert abs(e - oracle.energy(ref)) / E0 < 2e-12
+        od = oracle.divB(ref)
+        assert abs(dv[0] - od[0]) <= 1e-10 * od[0] and abs(dv[1] - od[1]) <= 1e-12 and abs(dv[2] - od[2]) <= 1e-12
+    else:
+        assert rel_l2(got, ref) < 2e-5
+        assert abs(e - oracle.energy(ref)) / E0 < 2e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_diagnostics_match_oracle(precision):
+    Nx, Ny = 333, 121
+    rng = np.random.default_rng(5)
+    q = rng.standard_normal((6, Ny, Nx))
+    if precision == "fp32":
+        q = q.astype(np.float32).astype(np.float64)
+    n = media.uniform_medium(Nx, Ny, (1.2, 1.3, 1.4))
+    with Simulation(*n, 0.1, precision=precision) as sim:
+        sim.set_fields(q)
+        d = sim.diagnostics()
+    assert d["nonfinite"] == 0
+    assert abs(d["energy"] - oracle.energy(q)) <= 1e-14 * oracle.energy(q)
+    s, m, b = oracle.divB(q)
+    assert abs(d["div_l2_sq"] - s) <= 1e-13 * s
+    assert abs(d["div_max"] - m) <= 1e-14 * m
+    assert abs(d["b_max"] - b) <= 1e-14 * b
+
+
+def test_diagnostics_deterministic():
+    Nx, Ny = 1000, 700
+    q = np.random.default_rng(9).standard_normal((6, Ny, Nx))
+    n = media.uniform_medium(Nx, Ny, (1.2, 1.3, 1.4))
+    with Simulation(*n, 0.1) as sim:
+        sim.set_fields(q)
+        a = [sim.diagnostics()["energy"] for _ in range(3)]
+    assert a[0] == a[1] == a[2]
+
+
+@pytest.mark.parametrize("family", ["TE", "TM"])
+def test_families_never_couple_bit_exact(family):
+    Nx, Ny = 300, 90
+    n, q0 = problem(Nx, Ny, seed=7)
+    te, tm = [0, 1, 5], [2, 3, 4]
+    zero = tm if family == "TE" else te
+    q0[zero] = 0.0
+    for pot in ("paper", "unitary"):
+        got = gpu_run(n, q0, 0.2, 17, precision="fp32", potential=pot)
+        assert all(np.abs(got[c]).max() == 0.0 for c in zero)
+
+
+def test_unitary_fp32_energy_drift_small():
+    """All operators orthogonal: FP32 energy drift is rounding only."""
+    w = media.workload_cylinder_256()
+    n = w.medium()
+    with Simulation(*n, w.delta, precision="fp32", potential="unitary") as sim:
+        sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, 1.0)
+        e0 = sim.energy()
+        sim.step(2000)
+        e1 = sim.energy()
+    assert abs(e1 / e0 - 1) < 2e-6
+
+
+def test_nonfinite_state_is_reported():
+    Nx, Ny = 64, 32
+    n = media.uniform_medium(Nx, Ny, (1.2, 1.3, 1.4))
+    q = np.zeros((6, Ny, Nx))
+    q[3, 5, 7] = np.nan
+    q[1, 2, 3] = np.inf
+    with Simulation(*n, 0.1) as sim:
+        sim.set_fields(q)
+        d = sim.diagnostics()
+        assert d["status"] == "QLA_ENONFINITE" and d["nonfinite"] == 2
+        sim.step(4)  # the context stays usable (not sticky)
+        sim.set_fields(np.zeros((6, Ny, Nx)))
+        assert sim.diagnostics()["status"] == "QLA_OK"
+
+
+def test_invalid_arguments_raise():
+    Nx, Ny = 16, 16
+    n = media.uniform_medium(Nx, Ny, (1.2, 1.3, 1.4))
+    with pytest.raises(QLAError):
+        Simulation(*n, 0.0)
+    with pytest.raises(QLAError):
+        Simulation(*n, 0.1, steps_per_pass=3)
+    with Simulation(*n, 0.1) as sim:
+        with pytest.raises(QLAError):
+            sim.step(-1)
+        with pytest.raises(QLAError):
+            sim.init_pulse("Ez", 3.0, -1.0)
+        sim.step(1)
+
+
+def test_step_count_and_zero_steps():
+    n, q0 = problem(40, 40)
+    with Simulation(*n, 0.2) as sim:
+        sim.set_fields(q0)
+        sim.step(0)
+        assert sim.step_count == 0
+        assert rel_l2(sim.get_fields(), q0.astype(np.float32).astype(np.float64)) == 0.0
+        sim.step(7)
+        assert sim.step_count == 7
+
+
+# ---------------------------------------------------------------------------
+# Full-size workload, in the launch configuration the benchmark times, on
+# sampled sites the oracle computes from a local window (the dependency radius
+# of one step is 4 sites along each axis, so after s steps a site depends only
+# on the (8s+1)^2 window around it).
+# ---------------------------------------------------------------------------
+
+def window(a, yc, xc, H):
+    Ny, Nx = a.shape[-2:]
+    ys = np.arange(yc - H, yc + H + 1) % Ny
+    xs = np.arange(xc - H, xc + H + 1) % Nx
+    return np.ascontiguousarray(a[..., ys[:, None], xs[None, :]])
+
+
+def test_cylinders_8192_sampled_parity():
+    w = media.workload_cylinders_8192()
+    n = w.medium()
+    steps = 8  # two fused passes of 4 steps
+    with Simulation(*n, w.delta, precision="fp32") as sim:
+        assert sim.steps_per_pass == 4
+        sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+        q0 = sim.get_fields()
+        sim.step(steps)
+        got = sim.get_fields(dtype=np.float32)
+    H = 4 * steps + 8
+    # sample sites: pulse flank, object edges, lattice corners (periodic wrap), strip/tile seams
+    obj = w.objects[0]
+    samples = [(4096, 1024 + 100), (0, 0), (8191, 8191), (int(obj.cy), int(obj.cx - obj.a)),
+               (int(obj.cy + obj.b), int(obj.cx)), (1234, 224), (4096, 223), (8000, 8180)]
+    for yc, xc in samples:
+        nw = tuple(window(a, yc, xc, H) for a in n)
+        qw = window(q0, yc, xc, H)
+        ref = oracle_run(nw, qw, w.delta, steps)
+        r = 3
+        a = window(got, yc, xc, r)
+        b = ref[:, H - r:H + r + 1, H - r:H + r + 1]
+        scale = max(np.abs(b).max(), 1e-3)
+        assert np.abs(a - b).max() <= 2e-6 * scale + 1e-12, (yc, xc)
