@@ -155,6 +155,30 @@ typedef struct {
 
 qla_status qla_diagnostics(qla_ctx *ctx, qla_diag *out);
 
+/* The same diagnostics for a state the caller holds in device memory, with no
+ * context and no device allocation. The paper has no counterpart: this exists
+ * for callers that may not call cudaMalloc when they need the diagnostics (an
+ * application whose device memory all belongs to its own allocator, or a loop
+ * that must not block on or fail in the allocator). Its scratch is a fixed
+ * 256 KB array in device memory that the library reserves on every GPU that
+ * loads it, for the life of the process.
+ * q: device pointer to [6][Ny][Nx] float (precision QLA_FP32) or double
+ *    (QLA_FP64) on the current device; read only. out: host struct, written.
+ * stream: cudaStream_t to run on (NULL = the legacy default stream); the call
+ *    synchronises it before returning.
+ * Limit: Ny <= 16384 (4 rows per partial record, 4096 records); a taller
+ * lattice, Nx*Ny > 2^31-1, a NULL pointer or a bad precision returns
+ * QLA_EINVAL without touching the GPU. CUDA failures return QLA_ECUDA.
+ * Non-finite values return QLA_ENONFINITE with *out filled in.
+ * The first call on each device looks up the array's device address (and may
+ * load the module): make it before any stream capture begins. All calls share
+ * the one array and it keeps the last call's contents (each call writes every
+ * record it reads, so nothing needs clearing); calls whose kernels overlap on
+ * the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller. Sums are taken in a fixed order that differs from
+ * qla_diagnostics, so the two agree to rounding (~1e-15 relative), not bitwise. */
+qla_status qla_diagnostics_noalloc(const void *q, int precision, int Nx, int Ny, void *stream, qla_diag *out);
+
 /* Copy the state to a caller-owned host array [6][Ny][Nx] of double
  * (or float). Synchronous. */
 qla_status qla_get_fields(qla_ctx *ctx, double *q);

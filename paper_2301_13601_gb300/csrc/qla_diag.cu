@@ -161,3 +161,102 @@ cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, voi
 }
 
 }  // namespace qla
+
+// ---------------------------------------------------------------------------
+// Allocation-free diagnostics (qla_diagnostics_noalloc in include/qla.h).
+//
+// Some callers cannot allocate device memory at the point where they need
+// the diagnostics: an application that hands all of the GPU's memory to its
+// own allocator up front (a framework's caching pool, a fixed budget per job)
+// and forbids cudaMalloc afterwards, or a monitoring loop that must not block
+// on the allocator or fail with out-of-memory halfway through a long run. This variant
+// runs the same two reduction kernels as the context-based diagnostics, but
+// keeps their scratch (the per-block partial records and the final result) in
+// the file-scope device array below instead of memory from cudaMalloc.
+//
+// The array is reserved in every GPU that loads the library, for the life of
+// the process. All calls share it and it keeps the previous call's contents:
+// every record a call reads is written earlier in the same call, so nothing
+// has to be cleared, but two calls whose kernels overlap on the GPU (different
+// streams, or different host threads) race on it.
+// ---------------------------------------------------------------------------
+#include <limits.h>
+
+#include <mutex>
+
+#include "../../include/qla.h"
+
+namespace qla {
+namespace {
+
+constexpr int NOALLOC_ROWS_PER_BLOCK = 4;
+constexpr int NOALLOC_MAX_PARTIALS = 4096;  // lattices of at most 4096 * 4 = 16384 rows
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+struct NoallocScratch {
+    Partial part[NOALLOC_MAX_PARTIALS];
+    DiagResult result;
+};
+
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+std::mutex g_noalloc_mu;
+NoallocScratch *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the array on the current device. In host code the
+// symbol g_noalloc_scratch is only a host-side stand-in, so the address is
+// looked up once per device (the first call on each device does this, and may
+// load the module; make that first call before any stream capture).
+cudaError_t noalloc_scratch(NoallocScratch **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<NoallocScratch *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace qla
+
+extern "C" qla_status qla_diagnostics_noalloc(const void *q, int precision, int Nx, int Ny, void *stream,
+                                              qla_diag *out) {
+    using namespace qla;
+    if (!q || !out || Nx < 1 || Ny < 1 || (long long)Nx * (long long)Ny > INT_MAX ||
+        (precision != QLA_FP32 && precision != QLA_FP64))
+        return QLA_EINVAL;
+    const int G = (Ny + NOALLOC_ROWS_PER_BLOCK - 1) / NOALLOC_ROWS_PER_BLOCK;
+    if (G > NOALLOC_MAX_PARTIALS) return QLA_EINVAL;  // Ny above 16384: the static scratch is too small
+    NoallocScratch *s = nullptr;
+    if (noalloc_scratch(&s) != cudaSuccess) {
+        cudaGetLastError();
+        return QLA_ECUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (precision == QLA_FP32)
+        diag_partial<float><<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, s->part);
+    else
+        diag_partial<double><<<G, DIAG_THREADS, 0, st>>>(static_cast<const double *>(q), Nx, Ny, s->part);
+    if (cudaGetLastError() != cudaSuccess) return QLA_ECUDA;
+    diag_final<<<1, DIAG_THREADS, 0, st>>>(s->part, G, &s->result);
+    if (cudaGetLastError() != cudaSuccess) return QLA_ECUDA;
+    DiagResult r;
+    if (cudaMemcpyAsync(&r, &s->result, sizeof(r), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return QLA_ECUDA;
+    }
+    out->energy = r.energy_sum / (double(Nx) * double(Ny));
+    out->div_l2_sq = r.div_sq_sum;
+    out->div_max = r.div_max;
+    out->b_max = r.b_max;
+    out->nonfinite = (long long)r.nonfinite;
+    return r.nonfinite ? QLA_ENONFINITE : QLA_OK;
+}

@@ -30,7 +30,7 @@ EXPORTS = [
     "qla_default_options", "qla_query_buffer_sizes", "qla_create", "qla_init_pulse", "qla_set_fields",
     "qla_set_fields_f32", "qla_step", "qla_energy", "qla_divB", "qla_diagnostics", "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
-    "qla_last_error", "qla_status_string", "qla_destroy",
+    "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc",
 ]
 
 
@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH):
     L.qla_status_string.restype = ctypes.c_char_p
     L.qla_destroy.argtypes = [v]
     L.qla_destroy.restype = None
+    L.qla_diagnostics_noalloc.argtypes = [v, i, i, i, v, P(Diag)]
+    L.qla_diagnostics_noalloc.restype = st
     _lib = L
     return L
 
