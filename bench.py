@@ -30,6 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes per sweep launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the default workload; valid only for the kernel source it was measured on
+# (profiles/sweep_kernel_cylinders8192_launches.md).
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "1450553662fbe268", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 4, "bytes_per_launch": 5.536e9 + 1.592e9}
+
 METRIC = "site-updates/s per QLA step"
 UNIT = "site-updates/s"
 BYTES_PER_SITE_UPDATE = 60.0  # FP32 general kernel: 24 B state read + 24 B write + 12 B n_x, n_y, n_z
@@ -188,11 +194,13 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     _build.build()
-    w = media.workload_cylinders_8192()
+    w = {"cylinders8192": media.workload_cylinders_8192, "ellipse2048": media.workload_ellipse_2048,
+         "cylinder256": media.workload_cylinder_256}[args.workload]()
     n = w.medium()
     S = QLA_STEPS_PER_BENCH_STEP
-    sim = Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass)
-    sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+    sim = Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
+                     chunk_rows=args.chunk_rows)
+    sim.init_pulse("Ez" if w.pulse.pol == media.POL_EZ else "Ey", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
     stream = sim.stream
     sites = w.Nx * w.Ny
 
@@ -235,18 +243,20 @@ def run_ours(args):
     launches_per_step = math.ceil(S / sim.steps_per_pass)
     # e2e through the public API with host buffers: pinned H2D state copy,
     # qla_step, diagnostics, D2H state copy, every bench step
-    host = torch.empty((6, w.Ny, w.Nx), dtype=torch.float32, pin_memory=True)
-    sim.get_fields_host_f32(host.data_ptr())
-    e2e_steps = max(2, min(args.steps, 5))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        sim.set_fields_host_f32(host.data_ptr())
-        sim.step(S)
-        sim.diagnostics()
+    e2e_value = None
+    if not args.skip_extras:
+        host = torch.empty((6, w.Ny, w.Nx), dtype=torch.float32, pin_memory=True)
         sim.get_fields_host_f32(host.data_ptr())
-    e2e_s = time.perf_counter() - t0
-    e2e_value = sites * S * e2e_steps * world / e2e_s
+        e2e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sim.set_fields_host_f32(host.data_ptr())
+            sim.step(S)
+            sim.diagnostics()
+            sim.get_fields_host_f32(host.data_ptr())
+        e2e_s = time.perf_counter() - t0
+        e2e_value = sites * S * e2e_steps * world / e2e_s
     sim.close()
     if rank != 0:
         if world > 1:
@@ -254,19 +264,26 @@ def run_ours(args):
         return
     peak, peak_kind = measured_peaks()
     k = sim.steps_per_pass
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", "qla_sweep.cuh"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    traffic = None
+    if (sha == MEASURED_TRAFFIC["sweep_sha256_prefix"] and w.name == MEASURED_TRAFFIC["workload"]
+            and k == MEASURED_TRAFFIC["steps_per_pass"]):
+        traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     launch_ms = sweep_ms / (args.steps * launches_per_step)
     achieved = BYTES_PER_SITE_UPDATE * sites * k / (launch_ms / 1e3) / 1e9
-    cb, _, _ = cpu_baseline(seconds=args.cpu_seconds)
+    cb = None if args.skip_extras else cpu_baseline(seconds=args.cpu_seconds)[0]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "cylinders8192_fp32", "lattice": f"{w.Nx}x{w.Ny}", "delta": w.delta,
+        "config": {"workload": w.name, "lattice": f"{w.Nx}x{w.Ny}", "delta": w.delta,
                    "qla_steps_per_bench_step": S, "steps_per_pass": k, "chunk_rows": sim.chunk_rows,
                    "precision": "fp32", "sequence": "interleaved", "potential": "paper",
                    "l2": "inputs larger than L2 (state 1.6 GB)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": f"sweep_kernel<float,{k}>", "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
                      "note": "algorithmic bytes of the unfused step x steps fused per launch"},
         "cpu_baseline": cb,
@@ -289,6 +306,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["cylinders8192", "ellipse2048", "cylinder256"], default="cylinders8192")
+    ap.add_argument("--chunk-rows", type=int, default=0)
+    ap.add_argument("--skip-extras", action="store_true", help="no e2e leg and no CPU baseline (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

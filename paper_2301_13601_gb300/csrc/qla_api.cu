@@ -101,7 +101,7 @@ int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
     const int W = qla::sweep_strip_width();
     const int wv = W - 8 * K;
     const int nsx = (Nx + wv - 1) / wv;
-    const int occ = prec ? qla::sweep_occupancy_f64(K) : qla::sweep_occupancy_f32(K);
+    const int occ = prec ? qla::sweep_occupancy_f64(K, 1) : qla::sweep_occupancy_f32(K, 1);
     const long long slots = (long long)sms * occ;
     double best = 1e300;
     int best_chunk = Ny;

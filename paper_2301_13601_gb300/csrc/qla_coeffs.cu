@@ -45,8 +45,10 @@ __device__ void tuned_pair_f32(double ang, float &mf, float &sf) {
     sf = __int_as_float(si + bds);
 }
 
+// Writes the pair (cos(ang) - 1, sin(ang)) of site i into pair plane `pair`.
 template <typename T>
-__device__ void store_rot(T *coef, size_t P, int pm, int ps, size_t i, double ang, bool tune) {
+__device__ void store_rot(T *coef, size_t P, int pair, size_t i, double ang, bool tune) {
+    T *dst = coef + 2 * (size_t(pair) * P + i);
     if constexpr (sizeof(T) == 4) {
         float mf, sf;
         if (tune) {
@@ -56,12 +58,12 @@ __device__ void store_rot(T *coef, size_t P, int pm, int ps, size_t i, double an
             mf = (float)(-2.0 * sh * sh);
             sf = (float)sin(ang);
         }
-        coef[size_t(pm) * P + i] = mf;
-        coef[size_t(ps) * P + i] = sf;
+        dst[0] = mf;
+        dst[1] = sf;
     } else {
         const double sh = sin(0.5 * ang);
-        coef[size_t(pm) * P + i] = -2.0 * sh * sh;
-        coef[size_t(ps) * P + i] = sin(ang);
+        dst[0] = -2.0 * sh * sh;
+        dst[1] = sin(ang);
     }
 }
 
@@ -92,14 +94,13 @@ __global__ void coef_kernel(const double *__restrict__ n, T *__restrict__ coef, 
         const double b2 = delta * delta * dnz_dx / (vnz * vnz);
         const double b3 = delta * delta * dnz_dy / (vnz * vnz);
         const bool tune_v = unitary != 0;  // the printed potentials are not rotations
-        store_rot<T>(coef, P, C_TM_M, C_TM_S, i, th2, true);
-        store_rot<T>(coef, P, C_TE_XM, C_TE_XS, i, th1, true);
-        store_rot<T>(coef, P, C_TE_YM, C_TE_YS, i, th0, true);
-        // potential planes: (sin b, cos b - 1) stored as (s plane, c plane)
-        store_rot<T>(coef, P, C_TM_VXC, C_TM_VXS, i, b2 * vscale, tune_v);
-        store_rot<T>(coef, P, C_TM_VYC, C_TM_VYS, i, b3 * vscale, tune_v);
-        store_rot<T>(coef, P, C_TE_VXC, C_TE_VXS, i, b0 * vscale, tune_v);
-        store_rot<T>(coef, P, C_TE_VYC, C_TE_VYS, i, b1 * vscale, tune_v);
+        store_rot<T>(coef, P, P_TM_C, i, th2, true);
+        store_rot<T>(coef, P, P_TE_CX, i, th1, true);
+        store_rot<T>(coef, P, P_TE_CY, i, th0, true);
+        store_rot<T>(coef, P, P_TM_VX, i, b2 * vscale, tune_v);
+        store_rot<T>(coef, P, P_TM_VY, i, b3 * vscale, tune_v);
+        store_rot<T>(coef, P, P_TE_VX, i, b0 * vscale, tune_v);
+        store_rot<T>(coef, P, P_TE_VY, i, b1 * vscale, tune_v);
     }
 }
 

@@ -6,28 +6,22 @@
 
 namespace qla {
 
-// Coefficient planes ([NCOEF][Ny][Nx], element type = state precision).
-// m = cos(angle) - 1, s = sin(angle) for the collision angles (Eq. 24);
-// vs = sin(b), vc = cos(b) - 1 for the effective potential angle b (Eq. 25,
-// scaled by 1/2 when interleaved (Eq. 28) and by 1/2 again for the unitary
-// potentials). Signs of the operators are applied by the kernels.
-enum CoefPlane {
-    C_TM_M = 0,   // theta_2 (x and y collisions of the TM family)
-    C_TM_S = 1,
-    C_TM_VXS = 2, // beta_2 (V_X row q4)
-    C_TM_VXC = 3,
-    C_TM_VYS = 4, // beta_3 (V_Y row q3)
-    C_TM_VYC = 5,
-    C_TE_XM = 6,  // theta_1 (C_X pair q1, q5)
-    C_TE_XS = 7,
-    C_TE_YM = 8,  // theta_0 (C_Y pair q0, q5)
-    C_TE_YS = 9,
-    C_TE_VXS = 10, // beta_0 (V_X row q5)
-    C_TE_VXC = 11,
-    C_TE_VYS = 12, // beta_1 (V_Y row q5)
-    C_TE_VYC = 13,
-    NCOEF = 14
+// Coefficient pair planes: NPAIR planes of [Ny][Nx] pairs (x = cos(a) - 1,
+// y = sin(a)), element type = state precision. The angle a is a collision
+// angle (Eq. 24) or an effective potential angle b (Eq. 25, scaled by 1/2
+// when interleaved (Eq. 28) and by 1/2 again for the unitary potentials).
+// Signs of the operators are applied by the kernels.
+enum CoefPair {
+    P_TM_C = 0,   // theta_2 (x and y collisions of the TM family)
+    P_TM_VX = 1,  // beta_2 (V_X row q4)
+    P_TM_VY = 2,  // beta_3 (V_Y row q3)
+    P_TE_CX = 3,  // theta_1 (C_X pair q1, q5)
+    P_TE_CY = 4,  // theta_0 (C_Y pair q0, q5)
+    P_TE_VX = 5,  // beta_0 (V_X row q5)
+    P_TE_VY = 6,  // beta_1 (V_Y row q5)
+    NPAIR = 7
 };
+constexpr int NCOEF = 2 * NPAIR;  // scalars per site
 
 // The six components split into two families that never couple (every
 // operator of Eq. 17-22 acts inside one of them):
@@ -37,10 +31,9 @@ enum CoefPlane {
 // moves the partner and the second (S_25) moves the hub.
 struct Family {
     int h, px, py;            // state planes
-    int cxm, cxs, cym, cys;   // collision coefficient planes
-    int vxs, vxc, vys, vyc;   // potential coefficient planes
-    float sgx, sgy;           // collision orientation: C acts as h += s h*m... see kernel
-    float tx, ty;             // potential orientation
+    int cx, cy, vx, vy;       // coefficient pair planes
+    float sgx, sgy;           // collision orientation: C is h' = h + (m h + sg sin p)
+    float tx, ty;             // potential orientation: target' = ... + t sin source
     int vx_hub, vy_hub;       // 1 if the potential row targets the hub, 0 if the partner
 };
 
@@ -63,8 +56,8 @@ cudaError_t launch_sweep_f32(int K, const SweepArgs &a, int nfam, cudaStream_t s
 cudaError_t launch_sweep_f64(int K, const SweepArgs &a, int nfam, cudaStream_t st);
 bool sweep_supported(int precision, int K);
 int sweep_strip_width();  // input columns per strip (halo included)
-int sweep_occupancy_f32(int K);  // resident CTAs per SM
-int sweep_occupancy_f64(int K);
+int sweep_occupancy_f32(int K, int interleaved);  // resident CTAs per SM
+int sweep_occupancy_f64(int K, int interleaved);
 
 // Coefficients (Eq. 24-25) from the device index planes n[3][Ny][Nx] (double).
 cudaError_t launch_coefficients(const double *n, void *coef, int Nx, int Ny, double delta,

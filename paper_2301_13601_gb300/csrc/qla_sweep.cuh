@@ -11,7 +11,8 @@
 //  * The six components form two families that never couple (TM: q2 hub, q4
 //    x-partner, q3 y-partner; TE: q5 hub, q1 x-partner, q0 y-partner). Every
 //    x-operator acts on (hub, x-partner) and every y-operator on
-//    (hub, y-partner). One CTA advances one family of one tile.
+//    (hub, y-partner). One CTA advances one family of one tile; the family,
+//    the step order and the potential variant are compile-time parameters.
 //  * A tile is a strip of W_IN = 256 columns (each lane of a warp holds 8
 //    consecutive columns) swept downwards over a chunk of rows. The strip
 //    carries a 4K-column halo on each side (a step has dependency radius 4
@@ -23,11 +24,17 @@
 //    registers per column, output trails input by 4 rows, and no y-halo is
 //    recomputed. The y-pass of level j writes level j+1's row buffer (double
 //    buffered) or, for the last level, global memory.
-//  * Level 0 rows are fetched one iteration ahead with cp.async.
+//  * No compute phase touches global memory for its inputs: the y-pass
+//    coefficients of an iteration are copied into shared memory with cp.async
+//    while the x-pass of that iteration runs, and the x-pass coefficients and
+//    next level-0 rows while the y-pass of the previous iteration runs. Rows
+//    are bulk-prefetched into L2 two iterations ahead.
 //  * Rotations use the (cos-1, sin) form h' = h + (m h + s p): one rounding at
-//    the scale of h per output, and coefficients whose FP32 norm error is
-//    minimised at creation.
+//    the scale of h per output, with coefficients whose FP32 norm error is
+//    minimised at creation. Coefficients are stored as (m, s) pairs.
 #pragma once
+
+#include <type_traits>
 
 #include "qla_internal.h"
 
@@ -38,52 +45,83 @@ constexpr int W_IN = 32 * LANE_COLS;
 
 struct SweepParams {
     SweepArgs a;
-    Family fam[2];
 };
 
 template <typename T>
 struct Ar;
 template <>
 struct Ar<float> {
+    using T2 = float2;
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
 };
 template <>
 struct Ar<double> {
+    using T2 = double2;
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
 };
 
+// Compile-time description of a family (see qla_internal.h).
+//   TM: hub q2, x-partner q4, y-partner q3.
+//     C_X on (q2,q4): q2' = c q2 - s q4 -> orientation -1; V_X row q4 <- -sin b2 q2 (partner, -1)
+//     C_Y on (q2,q3): q2' = c q2 + s q3 -> orientation +1; V_Y row q3 <- +sin b3 q2 (partner, +1)
+//   TE: hub q5, x-partner q1, y-partner q0.
+//     C_X on (q1,q5): q5' = s q1 + c q5 -> orientation +1; V_X row q5 <- +sin b0 q1 (hub, +1)
+//     C_Y on (q0,q5): q5' = -s q0 + c q5 -> orientation -1; V_Y row q5 <- -sin b1 q0 (hub, -1)
+template <int FAM>
+struct Fam;
+template <>
+struct Fam<0> {
+    static constexpr int H = 2, PX = 4, PY = 3;
+    static constexpr int CX = P_TM_C, CY = P_TM_C, VX = P_TM_VX, VY = P_TM_VY;
+    static constexpr int SGX = -1, SGY = +1, TX = -1, TY = +1;
+    static constexpr bool VX_HUB = false, VY_HUB = false;
+};
+template <>
+struct Fam<1> {
+    static constexpr int H = 5, PX = 1, PY = 0;
+    static constexpr int CX = P_TE_CX, CY = P_TE_CY, VX = P_TE_VX, VY = P_TE_VY;
+    static constexpr int SGX = +1, SGY = -1, TX = +1, TY = -1;
+    static constexpr bool VX_HUB = true, VY_HUB = true;
+};
+
 // Collision C (DAG = false) or its transpose (DAG = true) on (h, p), with
-// m = cos(theta) - 1 and s = orientation * sin(theta):
-//   C:  h' = h + (m h + s p),   p' = p + (m p - s h)
-template <bool DAG, typename T>
+// m = cos(theta) - 1, s = sin(theta) and orientation SG:
+//   C:  h' = h + (m h + SG s p),   p' = p + (m p - SG s h)
+template <bool DAG, int SG, typename T>
 __device__ __forceinline__ void rot(T &h, T &p, T m, T s) {
     using A = Ar<T>;
-    const T sg = DAG ? -s : s;
-    const T u = A::fma(m, h, A::mul(sg, p));
-    const T v = A::fma(m, p, -A::mul(sg, h));
+    constexpr bool pos = (SG > 0) != DAG;
+    const T sp = A::mul(s, p);
+    const T sh = A::mul(s, h);
+    const T u = pos ? A::fma(m, h, sp) : A::fma(m, h, -sp);
+    const T v = pos ? A::fma(m, p, -sh) : A::fma(m, p, sh);
     h = A::add(h, u);
     p = A::add(p, v);
 }
 
-// Potential row: target' = target + (c target + s source) with
-// s = orientation * sin(b), c = cos(b) - 1; the unitary variant also rotates the
-// source: source' = source + (c source - s target).
-template <typename T>
-__device__ __forceinline__ void vop(T &target, T &source, T s, T c, bool unitary) {
+// Potential row: target' = target + (c target + TAU s source), c = cos(b) - 1,
+// s = sin(b); the unitary variant also rotates the source:
+// source' = source + (c source - TAU s target).
+template <int TAU, bool UNIT, typename T>
+__device__ __forceinline__ void vop(T &target, T &source, T s, T c) {
     using A = Ar<T>;
-    const T t2 = A::add(target, A::fma(c, target, A::mul(s, source)));
-    if (unitary) source = A::add(source, A::fma(c, source, -A::mul(s, target)));
+    const T ss = A::mul(s, source);
+    const T t2 = A::add(target, TAU > 0 ? A::fma(c, target, ss) : A::fma(c, target, -ss));
+    if (UNIT) {
+        const T st = A::mul(s, target);
+        source = A::add(source, TAU > 0 ? A::fma(c, source, -st) : A::fma(c, source, st));
+    }
     target = t2;
 }
 
-template <typename T>
-__device__ __forceinline__ void vop_pair(T &h, T &p, T s, T c, bool target_is_hub, bool unitary) {
-    if (target_is_hub) vop(h, p, s, c, unitary);
-    else vop(p, h, s, c, unitary);
+template <int TAU, bool HUB, bool UNIT, typename T>
+__device__ __forceinline__ void vop_pair(T &h, T &p, T s, T c) {
+    if (HUB) vop<TAU, UNIT>(h, p, s, c);
+    else vop<TAU, UNIT>(p, h, s, c);
 }
 
 // a(x) <- a(x-1) across the warp's 8*32 columns
@@ -108,45 +146,41 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     int r = i % n;
     return r < 0 ? r + n : r;
 }
-
-// 8 consecutive (periodic) elements of a global row starting at column c0.
-template <typename T>
-__device__ __forceinline__ void gload8(T (&v)[LANE_COLS], const T *__restrict__ row, int c0, int Nx, bool vec) {
-    if (vec) {
-        if constexpr (sizeof(T) == 4) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(row + c0));
-            int c1 = c0 + 4;
-            if (c1 >= Nx) c1 -= Nx;
-            const float4 b = __ldg(reinterpret_cast<const float4 *>(row + c1));
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                int c = c0 + 2 * k;
-                c = c >= Nx ? c - Nx * (c / Nx) : c;
-                const double2 d = __ldg(reinterpret_cast<const double2 *>(row + c));
-                v[2 * k] = d.x;
-                v[2 * k + 1] = d.y;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < LANE_COLS; ++j) v[j] = __ldg(row + (c0 + j) % Nx);
-    }
+__device__ __forceinline__ int wrap_down(int v, int n) {
+    while (v >= n) v -= n;
+    return v;
+}
+__device__ __forceinline__ int wrap_up(int v, int n) {
+    while (v < 0) v += n;
+    return v;
 }
 
+// Shared rows hold W_IN elements of type E. 16-byte chunks are XOR-swizzled
+// within groups of eight chunks (chunk c is stored at c ^ ((c >> 3) & MASK))
+// so that both access patterns are free of bank conflicts: a lane reading its
+// 8 consecutive columns with 16-byte loads, and a warp reading 32
+// consecutive columns one element per thread.
+template <typename E>
+__device__ __forceinline__ int swz(int e) {
+    constexpr int EPC = 16 / int(sizeof(E));
+    constexpr int MASK = sizeof(E) == 4 ? 1 : (sizeof(E) == 8 ? 3 : 7);
+    const int chunk = e / EPC;
+    return (chunk ^ ((chunk >> 3) & MASK)) * EPC + (e % EPC);
+}
+
+// The 8 consecutive columns of lane `lane` of a shared row.
 template <typename T>
-__device__ __forceinline__ void sload8(T (&v)[LANE_COLS], const T *p) {
+__device__ __forceinline__ void sload8(T (&v)[LANE_COLS], const T *row, int lane) {
+    const int c0 = LANE_COLS * lane;
     if constexpr (sizeof(T) == 4) {
-        const float4 a = *reinterpret_cast<const float4 *>(p);
-        const float4 b = *reinterpret_cast<const float4 *>(p + 4);
+        const float4 a = *reinterpret_cast<const float4 *>(row + swz<T>(c0));
+        const float4 b = *reinterpret_cast<const float4 *>(row + swz<T>(c0 + 4));
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const double2 d = *reinterpret_cast<const double2 *>(p + 2 * k);
+            const double2 d = *reinterpret_cast<const double2 *>(row + swz<T>(c0 + 2 * k));
             v[2 * k] = d.x;
             v[2 * k + 1] = d.y;
         }
@@ -154,13 +188,40 @@ __device__ __forceinline__ void sload8(T (&v)[LANE_COLS], const T *p) {
 }
 
 template <typename T>
-__device__ __forceinline__ void sstore8(T *p, const T (&v)[LANE_COLS]) {
+__device__ __forceinline__ void sstore8(T *row, int lane, const T (&v)[LANE_COLS]) {
+    const int c0 = LANE_COLS * lane;
     if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        *reinterpret_cast<float4 *>(row + swz<T>(c0)) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(row + swz<T>(c0 + 4)) = make_float4(v[4], v[5], v[6], v[7]);
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) *reinterpret_cast<double2 *>(p + 2 * k) = make_double2(v[2 * k], v[2 * k + 1]);
+        for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<double2 *>(row + swz<T>(c0 + 2 * k)) = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+
+// 8 coefficient pairs (x = m, y = s) of lane `lane` from a shared pair row.
+template <typename T>
+__device__ __forceinline__ void sload8pair(T (&m)[LANE_COLS], T (&s)[LANE_COLS], const typename Ar<T>::T2 *row,
+                                           int lane) {
+    using T2 = typename Ar<T>::T2;
+    const int c0 = LANE_COLS * lane;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(row + swz<T2>(c0 + 2 * k));
+            m[2 * k] = v.x;
+            s[2 * k] = v.y;
+            m[2 * k + 1] = v.z;
+            s[2 * k + 1] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < LANE_COLS; ++k) {
+            const double2 v = row[swz<T2>(c0 + k)];
+            m[k] = v.x;
+            s[k] = v.y;
+        }
     }
 }
 
@@ -175,48 +236,94 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// Hint: bring [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte aligned).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 
-// Register pipeline of the y-pass for one column of one level.
+// Copies the strip's 256 columns of one global row into a (swizzled) shared
+// row: lane l copies strip columns 8l .. 8l+7. xb: wrapped global column of
+// strip column 0; nowrap: the strip lies inside [0, Nx).
+template <typename E>
+__device__ __forceinline__ void copy_strip_row(E *dst, const E *grow, int xb, int Nx, bool nowrap, bool vec,
+                                               int lane) {
+    constexpr int EPC = 16 / int(sizeof(E));
+    const int c0 = LANE_COLS * lane;
+    if (vec) {
+#pragma unroll
+        for (int k = 0; k < LANE_COLS / EPC; ++k) {
+            const int sc = c0 + k * EPC;
+            const int gc = nowrap ? xb + sc : wrap_down(xb + sc, Nx);
+            cp_async16(dst + swz<E>(sc), grow + gc);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < LANE_COLS; ++e) {
+            const int sc = c0 + e;
+            cp_async_small<sizeof(E)>(dst + swz<E>(sc), grow + wrap_down(xb + sc, Nx));
+        }
+    }
+}
+
+template <typename T, int K, int R, bool INTER>
+struct SweepLayout {
+    using T2 = typename Ar<T>::T2;
+    static constexpr int NYS = INTER ? 2 : 3;  // y-pass pairs: C_Y, V_Y (+ V_X for Eq. 23)
+    static constexpr int NXS = INTER ? 2 : 1;  // x-pass pairs: C_X (+ V_X for Eq. 28)
+    static constexpr size_t STATE = size_t(K) * 2 * 3 * R * W_IN * sizeof(T);
+    static constexpr size_t YST = size_t(K) * NYS * R * W_IN * sizeof(T2);
+    static constexpr size_t XST = size_t(K) * NXS * R * W_IN * sizeof(T2);
+    static constexpr size_t SMEM = STATE + YST + XST;
+};
+
+template <typename T, int K, int R, int NY>
+struct SweepCfg {
+    static constexpr int NT = W_IN * K / NY;
+    // two resident CTAs per SM when the block is small and its shared memory allows it
+    static constexpr int MINB =
+        (sizeof(T) == 4 && NT <= 256 && SweepLayout<T, K, R, true>::SMEM <= 114 * 1024) ? 2 : 1;
+    static constexpr int NWARP = NT / 32;
+    static_assert(W_IN * K % NY == 0, "tasks must divide");
+    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+    static_assert(K * R <= NWARP * 4, "x-pass row tasks per warp");
+};
+
 template <typename T>
 struct YPipe {
     T S2, S4, S6, S8, S10, S12, S14, S16;  // one saved value per y-shift
     T m1, s1, m2, s2, m3, s3;              // collision coefficients of rows R-1, R-2, R-3
     T d0, d1, d2, d3;                      // x-partner delayed by 4 rows
+    T vc1, vs1, vc2, vs2, vc3, vs3, vc4, vs4;  // V_Y pair of rows R-1 .. R-4
+    T wc1, ws1, wc2, ws2, wc3, ws3, wc4, ws4;  // V_X pair of rows R-1 .. R-4 (Eq. 23 only)
     __device__ __forceinline__ void zero() {
         S2 = S4 = S6 = S8 = S10 = S12 = S14 = S16 = T(0);
         m1 = s1 = m2 = s2 = m3 = s3 = T(0);
         d0 = d1 = d2 = d3 = T(0);
+        vc1 = vs1 = vc2 = vs2 = vc3 = vs3 = vc4 = vs4 = T(0);
+        wc1 = ws1 = wc2 = ws2 = wc3 = ws3 = wc4 = ws4 = T(0);
     }
 };
 
-template <typename T, int K, int NY, int R>
-struct SweepCfg {
-    static constexpr int NT = W_IN * K / NY;
-    static constexpr int NWARP = NT / 32;
-    static constexpr size_t SMEM = size_t(K) * 2 * 3 * R * W_IN * sizeof(T);
-    static_assert(W_IN * K % NY == 0, "tasks must divide");
-    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
-};
-
-template <typename T, int K, int NY, int R>
-__global__ void __launch_bounds__(SweepCfg<T, K, NY, R>::NT, 1) sweep_kernel(const SweepParams prm) {
-    using Cfg = SweepCfg<T, K, NY, R>;
+template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
+__device__ __forceinline__ void sweep_body(const SweepArgs &A, unsigned char *smem_raw) {
+    using Cfg = SweepCfg<T, K, R, NY>;
+    using L = SweepLayout<T, K, R, INTER>;
+    using T2 = typename Ar<T>::T2;
+    using Fm = Fam<FAM>;
     constexpr int NT = Cfg::NT;
     constexpr int NWARP = Cfg::NWARP;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *const buf = reinterpret_cast<T *>(smem_raw);
+    constexpr int NYS = L::NYS, NXS = L::NXS;
 
-    const SweepArgs &A = prm.a;
-    Family F = prm.fam[0];
-    if (A.fam0 + int(blockIdx.z) == 1) F = prm.fam[1];
+    T *const buf = reinterpret_cast<T *>(smem_raw);
+    T2 *const yst = reinterpret_cast<T2 *>(smem_raw + L::STATE);
+    T2 *const xst = reinterpret_cast<T2 *>(smem_raw + L::STATE + L::YST);
+
     const int Nx = A.Nx, Ny = A.Ny;
-    const size_t P = size_t(Nx) * size_t(Ny);
+    const int P = Nx * Ny;  // < 2^31 (checked on the host)
     const T *__restrict__ qin = static_cast<const T *>(A.q_in);
     T *__restrict__ qout = static_cast<T *>(A.q_out);
-    const T *__restrict__ coef = static_cast<const T *>(A.coef);
+    const T2 *__restrict__ cpairs = static_cast<const T2 *>(A.coef);
     const bool vec = A.vec != 0;
-    const bool inter = A.interleaved != 0;
-    const bool unit = A.unitary != 0;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -224,54 +331,125 @@ __global__ void __launch_bounds__(SweepCfg<T, K, NY, R>::NT, 1) sweep_kernel(con
 
     const int xs0 = blockIdx.x * A.w_valid;   // first output column of the strip
     const int xbase = xs0 - 4 * K;            // global column of strip column 0 (may be < 0)
+    const int xb = wrapi(xbase, Nx);
+    const bool nowrap = xbase >= 0 && xbase + W_IN <= Nx;
     const int yb = blockIdx.y * A.chunk;
     const int ye = min(yb + A.chunk, Ny);
     const int F0 = yb - 4 * K;                // first row fed to level 0
     const int nit = (ye - yb + 8 * K + R - 1) / R + K - 1;
 
     auto bufrow = [&](int j, int half, int comp, int ir) -> T * {
-        return buf + ((size_t(((j * 2 + half) * 3 + comp) * R + ir)) * W_IN);
+        return buf + ((((j * 2 + half) * 3 + comp) * R + ir) * W_IN);
     };
-    // first row handled by level j in iteration it
+    auto ystrow = [&](int j, int slot, int ir) -> T2 * { return yst + (((j * NYS + slot) * R + ir) * W_IN); };
+    auto xstrow = [&](int j, int slot, int ir) -> T2 * { return xst + (((j * NXS + slot) * R + ir) * W_IN); };
+    // first (unwrapped) row handled by level j in iteration it
     auto arow = [&](int j, int it) { return F0 + (it - j) * R - 4 * j; };
     auto active = [&](int j, int it) { return it >= j && arow(j, it) <= ye - 1 + 4 * (K - j); };
-
-    for (int i = tid; i < K * 2 * 3 * R * W_IN; i += NT) buf[i] = T(0);
-
-    auto plane_of = [&](int comp) { return comp == 0 ? F.h : (comp == 1 ? F.px : F.py); };
-
-    auto load0 = [&](int it, int half) {
-        const int row0 = arow(0, it);
-        if (vec) {
-            constexpr int EPC = 16 / sizeof(T);
-            constexpr int CH = W_IN / EPC;
-            for (int q = tid; q < 3 * R * CH; q += NT) {
-                const int k = q % CH;
-                const int rc = q / CH;
-                const int ir = rc % R;
-                const int comp = rc / R;
-                const int grow = wrapi(row0 + ir, Ny);
-                const int gcol = wrapi(xbase + k * EPC, Nx);
-                const T *src = qin + size_t(plane_of(comp)) * P + size_t(grow) * Nx + gcol;
-                cp_async16(bufrow(0, half, comp, ir) + k * EPC, src);
-            }
-        } else {
-            for (int q = tid; q < 3 * R * W_IN; q += NT) {
-                const int c = q % W_IN;
-                const int rc = q / W_IN;
-                const int ir = rc % R;
-                const int comp = rc / R;
-                const int grow = wrapi(row0 + ir, Ny);
-                const int gcol = wrapi(xbase + c, Nx);
-                const T *src = qin + size_t(plane_of(comp)) * P + size_t(grow) * Nx + gcol;
-                cp_async_small<sizeof(T)>(bufrow(0, half, comp, ir) + c, src);
-            }
-        }
-        cp_async_commit();
+    // wrapped global row of row ir of level j in iteration it, from the
+    // wrapped first level-0 row of the current iteration (no division)
+    int itcur = 0, r0w = wrapi(F0, Ny);
+    auto growof = [&](int j, int it, int ir) {
+        return wrap_down(wrap_up(r0w + (it - itcur) * R - j * (R + 4) + ir, Ny), Ny);
     };
 
+    const T *const qh = qin + size_t(Fm::H) * P;
+    const T *const qpx = qin + size_t(Fm::PX) * P;
+    const T *const qpy = qin + size_t(Fm::PY) * P;
+    const T2 *const pCX = cpairs + size_t(Fm::CX) * P;
+    const T2 *const pCY = cpairs + size_t(Fm::CY) * P;
+    const T2 *const pVX = cpairs + size_t(Fm::VX) * P;
+    const T2 *const pVY = cpairs + size_t(Fm::VY) * P;
+
+    // Row segments copied per iteration are spread over the warps; a warp
+    // copies one 256-column row segment per task (each lane 8 columns).
+    // level-0 state rows for iteration it (3 components x R rows)
+    auto copy_state0 = [&](int it, int half) {
+        for (int task = warp; task < 3 * R; task += NWARP) {
+            const int comp = task / R, ir = task % R;
+            const T *src = (comp == 0 ? qh : (comp == 1 ? qpx : qpy)) + size_t(growof(0, it, ir)) * Nx;
+            copy_strip_row(bufrow(0, half, comp, ir), src, xb, Nx, nowrap, vec, lane);
+        }
+    };
+    // x-pass coefficient rows of iteration it, all active levels
+    auto copy_xstash = [&](int it) {
+        for (int task = warp; task < K * NXS * R; task += NWARP) {
+            const int j = task / (NXS * R), rem = task % (NXS * R);
+            const int slot = rem / R, ir = rem % R;
+            if (!active(j, it)) continue;
+            const T2 *plane = slot == 0 ? pCX : pVX;
+            copy_strip_row(xstrow(j, slot, ir), plane + size_t(growof(j, it, ir)) * Nx, xb, Nx, nowrap, vec, lane);
+        }
+    };
+    // y-pass coefficient rows of iteration it
+    auto copy_ystash = [&](int it) {
+        for (int task = warp; task < K * NYS * R; task += NWARP) {
+            const int j = task / (NYS * R), rem = task % (NYS * R);
+            const int slot = rem / R, ir = rem % R;
+            const T2 *plane = slot == 0 ? pCY : (slot == 1 ? pVY : pVX);
+            copy_strip_row(ystrow(j, slot, ir), plane + size_t(growof(j, it, ir)) * Nx, xb, Nx, nowrap, vec, lane);
+        }
+    };
+    // L2 prefetch of the level-0 rows of iteration it (state and coefficients)
+    auto prefetch_rows = [&](int it) {
+        constexpr int NPL = 3 + 4;
+        if (!vec || (xb & 1)) return;
+        for (int task = tid; task < R * NPL; task += NT) {
+            const int ir = task / NPL, k = task % NPL;
+            const int row = growof(0, it, ir);
+            const char *rowp;
+            int esz;
+            if (k < 3) {
+                rowp = reinterpret_cast<const char *>((k == 0 ? qh : (k == 1 ? qpx : qpy)) + size_t(row) * Nx);
+                esz = sizeof(T);
+            } else {
+                const T2 *pl = k == 3 ? pCX : (k == 4 ? pCY : (k == 5 ? pVX : pVY));
+                if (k == 4 && Fm::CX == Fm::CY) continue;
+                rowp = reinterpret_cast<const char *>(pl + size_t(row) * Nx);
+                esz = sizeof(T2);
+            }
+            if (W_IN >= Nx) {
+                prefetch_l2(rowp, unsigned(Nx * esz));
+            } else {
+                const int len1 = min(W_IN, Nx - xb);
+                prefetch_l2(rowp + size_t(xb) * esz, unsigned(len1 * esz));
+                if (len1 < W_IN) prefetch_l2(rowp, unsigned((W_IN - len1) * esz));
+            }
+        }
+    };
+
+    for (int i = tid; i < int(L::STATE / sizeof(T)); i += NT) buf[i] = T(0);
+
+    // ---- y-pass tasks: fixed (level, column) per thread slot ---------------
+    // Only the last slot can hold the last level (tasks are ordered by level).
+    constexpr int LVL = 2 * 3 * R * W_IN;   // elements of one level's state buffers
+    constexpr int HALF = 3 * R * W_IN;      // one half (3 components x R rows)
+    constexpr int YLVL = NYS * R * W_IN;    // one level's y-stash pairs
+    int yj[NY];
+    const T *st_base[NY];
+    const T2 *ys_base[NY];
+#pragma unroll
+    for (int u = 0; u < NY; ++u) {
+        const int task = tid + u * NT;
+        yj[u] = task / W_IN;
+        const int c = task % W_IN;
+        st_base[u] = buf + yj[u] * LVL + swz<T>(c);
+        ys_base[u] = yst + yj[u] * YLVL + swz<T2>(c);
+    }
+    const int c_last = (tid + (NY - 1) * NT) % W_IN;
+    const bool last_is_final = yj[NY - 1] == K - 1;  // uniform per warp
+    const bool col_ok = c_last >= 4 * K && c_last < 4 * K + A.w_valid && xs0 + (c_last - 4 * K) < Nx;
+    const int gx = xs0 - 4 * K + c_last;
+    T *const qo_h = qout + size_t(Fm::H) * P + gx;
+    T *const qo_px = qout + size_t(Fm::PX) * P + gx;
+    T *const qo_py = qout + size_t(Fm::PY) * P + gx;
+
     __syncthreads();  // zeroed buffers before the async copies land
-    load0(0, 0);
+    prefetch_rows(0);
+    prefetch_rows(1);
+    copy_state0(0, 0);
+    copy_xstash(0);
+    cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
 
@@ -279,207 +457,216 @@ __global__ void __launch_bounds__(SweepCfg<T, K, NY, R>::NT, 1) sweep_kernel(con
 #pragma unroll
     for (int u = 0; u < NY; ++u) yp[u].zero();
 
-    const T sgx = T(F.sgx), sgy = T(F.sgy), tx = T(F.tx), ty = T(F.ty);
-    const bool vxh = F.vx_hub != 0, vyh = F.vy_hub != 0;
-
     for (int it = 0; it < nit; ++it) {
         const int cur = it & 1;
-        if (it + 1 < nit && active(0, it + 1)) load0(it + 1, cur ^ 1);
+        prefetch_rows(it + 2);
+        copy_ystash(it);
+        cp_async_commit();
 
         // ---- phase 1: x-pass, one warp per (level, row) -------------------
         for (int task = warp; task < K * R; task += NWARP) {
-            const int j = task / R;
-            const int ir = task % R;
+            const int j = task / R, ir = task % R;
             if (!active(j, it)) continue;
-            T *rh = bufrow(j, cur, 0, ir) + LANE_COLS * lane;
-            T *rp = bufrow(j, cur, 1, ir) + LANE_COLS * lane;
-            const int grow = wrapi(arow(j, it) + ir, Ny);
-            const int gc0 = wrapi(xbase + LANE_COLS * lane, Nx);
-            const size_t roff = size_t(grow) * Nx;
+            T *rh = bufrow(j, cur, 0, ir);
+            T *rp = bufrow(j, cur, 1, ir);
             T m[LANE_COLS], s[LANE_COLS], h[LANE_COLS], p[LANE_COLS];
-            gload8(m, coef + size_t(F.cxm) * P + roff, gc0, Nx, vec);
-            gload8(s, coef + size_t(F.cxs) * P + roff, gc0, Nx, vec);
-            sload8(h, rh);
-            sload8(p, rp);
-#pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) s[c] *= sgx;
+            sload8pair(m, s, xstrow(j, 0, ir), lane);
+            sload8(h, rh, lane);
+            sload8(p, rp, lane);
+            constexpr int SG = Fm::SGX;
             // ops 1-8
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
             shift_from_left(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
             shift_from_right(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
             shift_from_right(h);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
             shift_from_left(h);
-            T vs[LANE_COLS], vc[LANE_COLS];
-            if (inter) {
-                gload8(vs, coef + size_t(F.vxs) * P + roff, gc0, Nx, vec);
-                gload8(vc, coef + size_t(F.vxc) * P + roff, gc0, Nx, vec);
+            T vc[LANE_COLS], vs[LANE_COLS];
+            if constexpr (INTER) {
+                sload8pair(vc, vs, xstrow(j, 1, ir), lane);
 #pragma unroll
-                for (int c = 0; c < LANE_COLS; ++c) {
-                    vs[c] *= tx;
-                    vop_pair(h[c], p[c], vs[c], vc[c], vxh, unit);
-                }
+                for (int c = 0; c < LANE_COLS; ++c) vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
             }
             // ops 9-16
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
             shift_from_right(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
             shift_from_left(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
             shift_from_left(h);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
             shift_from_right(h);
-            if (inter) {
+            if constexpr (INTER) {
 #pragma unroll
-                for (int c = 0; c < LANE_COLS; ++c) vop_pair(h[c], p[c], vs[c], vc[c], vxh, unit);
+                for (int c = 0; c < LANE_COLS; ++c) vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
             }
-            sstore8(rh, h);
-            sstore8(rp, p);
+            sstore8(rh, lane, h);
+            sstore8(rp, lane, p);
         }
+        cp_async_wait_all();
         __syncthreads();
 
+        // next iteration's x-pass coefficients and level-0 rows land while the
+        // y-pass runs
+        if (it + 1 < nit) {
+            copy_xstash(it + 1);
+            if (active(0, it + 1)) copy_state0(it + 1, cur ^ 1);
+        }
+        cp_async_commit();
+
         // ---- phase 2: y-pass, one thread per (level, column) --------------
-#pragma unroll
-        for (int u = 0; u < NY; ++u) {
-            const int task = tid + u * NT;
-            const int j = task / W_IN;
-            const int c = task % W_IN;
-            if (!active(j, it)) continue;
-            YPipe<T> &Y = yp[u];
-            const int gcol = wrapi(xbase + c, Nx);
-            const T *hin = bufrow(j, cur, 0, 0) + c;
-            const T *pxin = bufrow(j, cur, 1, 0) + c;
-            const T *pyin = bufrow(j, cur, 2, 0) + c;
-            const bool last = (j == K - 1);
-            T *hout = last ? nullptr : bufrow(j + 1, cur ^ 1, 0, 0) + c;
-            T *pxout = last ? nullptr : bufrow(j + 1, cur ^ 1, 1, 0) + c;
-            T *pyout = last ? nullptr : bufrow(j + 1, cur ^ 1, 2, 0) + c;
-            const bool col_ok = last && c >= 4 * K && c < 4 * K + A.w_valid && xs0 + (c - 4 * K) < Nx;
-            const int gx = xs0 + (c - 4 * K);
-            const T *cym = coef + size_t(F.cym) * P + gcol;
-            const T *cys = coef + size_t(F.cys) * P + gcol;
-            const T *vys = coef + size_t(F.vys) * P + gcol;
-            const T *vyc = coef + size_t(F.vyc) * P + gcol;
-            const T *vxs = coef + size_t(F.vxs) * P + gcol;
-            const T *vxc = coef + size_t(F.vxc) * P + gcol;
-            const int a0 = arow(j, it);
+        // The NY column pipelines of a thread advance row by row together so
+        // that their independent dependency chains interleave. A pipeline runs
+        // even in iterations where its level is inactive (before its first or
+        // after its last needed row): those rows are never read by a later
+        // level nor written to global memory, and running unconditionally
+        // keeps the loop-carried pipeline registers free of merge copies.
+        const int hin = cur * HALF, hout = (cur ^ 1) * HALF;
+        const int rout0 = arow(yj[NY - 1], it) - 4;  // first output row of the last slot
+        auto rows = [&](auto final_tag) {
+            constexpr bool FINAL = decltype(final_tag)::value;
 #pragma unroll
             for (int ir = 0; ir < R; ++ir) {
-                const int rin = a0 + ir;
-                const size_t o0 = size_t(wrapi(rin, Ny)) * Nx;
-                const size_t o2 = size_t(wrapi(rin - 2, Ny)) * Nx;
-                const size_t o4 = size_t(wrapi(rin - 4, Ny)) * Nx;
-                const T m0 = __ldg(cym + o0);
-                const T s0 = __ldg(cys + o0) * sgy;
-                T h = hin[ir * W_IN];
-                T p = pyin[ir * W_IN];
-                const T px0 = pxin[ir * W_IN];
-                rot<true>(h, p, m0, s0);                    // op 1  C+   (row R)
-                { const T t = Y.S2; Y.S2 = p; p = t; }      // op 2  p <- p(r-1)
-                rot<false>(h, p, m0, s0);                   // op 3  C    (row R)
-                { const T t = Y.S4; Y.S4 = h; h = t; }      // op 4  p <- p(r+1): now row R-1
-                rot<true>(h, p, Y.m1, Y.s1);                // op 5  C+   (row R-1)
-                { const T t = Y.S6; Y.S6 = p; p = t; }      // op 6  h <- h(r+1): now row R-2
-                rot<false>(h, p, Y.m2, Y.s2);               // op 7  C    (row R-2)
-                { const T t = Y.S8; Y.S8 = h; h = t; }      // op 8  h <- h(r-1)
-                if (inter) {
-                    const T vs = __ldg(vys + o2) * ty, vc = __ldg(vyc + o2);
-                    vop_pair(h, p, vs, vc, vyh, unit);      // V_Y' (row R-2)
-                }
-                rot<false>(h, p, Y.m2, Y.s2);               // op 9  C    (row R-2)
-                { const T t = Y.S10; Y.S10 = h; h = t; }    // op 10 p <- p(r+1): now row R-3
-                rot<true>(h, p, Y.m3, Y.s3);                // op 11 C+   (row R-3)
-                { const T t = Y.S12; Y.S12 = p; p = t; }    // op 12 p <- p(r-1)
-                rot<false>(h, p, Y.m3, Y.s3);               // op 13 C    (row R-3)
-                { const T t = Y.S14; Y.S14 = h; h = t; }    // op 14 h <- h(r-1)
-                rot<true>(h, p, Y.m3, Y.s3);                // op 15 C+   (row R-3)
-                { const T t = Y.S16; Y.S16 = p; p = t; }    // op 16 h <- h(r+1): now row R-4
-                T px = Y.d3;
-                Y.d3 = Y.d2; Y.d2 = Y.d1; Y.d1 = Y.d0; Y.d0 = px0;
-                if (inter) {
-                    const T vs = __ldg(vys + o4) * ty, vc = __ldg(vyc + o4);
-                    vop_pair(h, p, vs, vc, vyh, unit);      // V_Y' (row R-4)
-                } else {
-                    const T xs = __ldg(vxs + o4) * tx, xc = __ldg(vxc + o4);
-                    vop_pair(h, px, xs, xc, vxh, unit);     // V_X  (row R-4)
-                    const T vs = __ldg(vys + o4) * ty, vc = __ldg(vyc + o4);
-                    vop_pair(h, p, vs, vc, vyh, unit);      // V_Y  (row R-4)
-                }
-                Y.m3 = Y.m2; Y.s3 = Y.s2;
-                Y.m2 = Y.m1; Y.s2 = Y.s1;
-                Y.m1 = m0;   Y.s1 = s0;
-                if (!last) {
-                    hout[ir * W_IN] = h;
-                    pxout[ir * W_IN] = px;
-                    pyout[ir * W_IN] = p;
-                } else {
-                    const int rout = rin - 4;
-                    if (col_ok && rout >= yb && rout < ye) {
-                        const size_t o = size_t(rout) * Nx + gx;
-                        qout[size_t(F.h) * P + o] = h;
-                        qout[size_t(F.px) * P + o] = px;
-                        qout[size_t(F.py) * P + o] = p;
+#pragma unroll
+                for (int u = 0; u < NY; ++u) {
+                    YPipe<T> &Y = yp[u];
+                    constexpr int SG = Fm::SGY;
+                    const T *in = st_base[u] + hin;
+                    const T2 *ys = ys_base[u];
+                    const T2 cy = ys[(0 * R + ir) * W_IN];
+                    const T2 vy = ys[(1 * R + ir) * W_IN];
+                    const T m0 = cy.x, s0 = cy.y;
+                    T h = in[(0 * R + ir) * W_IN];
+                    T p = in[(2 * R + ir) * W_IN];
+                    const T px0 = in[(1 * R + ir) * W_IN];
+                    rot<true, SG>(h, p, m0, s0);                // op 1  C+   (row R)
+                    { const T t = Y.S2; Y.S2 = p; p = t; }      // op 2  p <- p(r-1)
+                    rot<false, SG>(h, p, m0, s0);               // op 3  C    (row R)
+                    { const T t = Y.S4; Y.S4 = h; h = t; }      // op 4  p <- p(r+1): now row R-1
+                    rot<true, SG>(h, p, Y.m1, Y.s1);            // op 5  C+   (row R-1)
+                    { const T t = Y.S6; Y.S6 = p; p = t; }      // op 6  h <- h(r+1): now row R-2
+                    rot<false, SG>(h, p, Y.m2, Y.s2);           // op 7  C    (row R-2)
+                    { const T t = Y.S8; Y.S8 = h; h = t; }      // op 8  h <- h(r-1)
+                    if constexpr (INTER)
+                        vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs2, Y.vc2);  // V_Y' (row R-2)
+                    rot<false, SG>(h, p, Y.m2, Y.s2);           // op 9  C    (row R-2)
+                    { const T t = Y.S10; Y.S10 = h; h = t; }    // op 10 p <- p(r+1): now row R-3
+                    rot<true, SG>(h, p, Y.m3, Y.s3);            // op 11 C+   (row R-3)
+                    { const T t = Y.S12; Y.S12 = p; p = t; }    // op 12 p <- p(r-1)
+                    rot<false, SG>(h, p, Y.m3, Y.s3);           // op 13 C    (row R-3)
+                    { const T t = Y.S14; Y.S14 = h; h = t; }    // op 14 h <- h(r-1)
+                    rot<true, SG>(h, p, Y.m3, Y.s3);            // op 15 C+   (row R-3)
+                    { const T t = Y.S16; Y.S16 = p; p = t; }    // op 16 h <- h(r+1): now row R-4
+                    T px = Y.d3;
+                    Y.d3 = Y.d2; Y.d2 = Y.d1; Y.d1 = Y.d0; Y.d0 = px0;
+                    if constexpr (INTER) {
+                        vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs4, Y.vc4);  // V_Y' (row R-4)
+                    } else {
+                        vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h, px, Y.ws4, Y.wc4);  // V_X  (row R-4)
+                        vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs4, Y.vc4);   // V_Y  (row R-4)
+                        const T2 vx = ys[(2 * R + ir) * W_IN];
+                        Y.wc4 = Y.wc3; Y.ws4 = Y.ws3; Y.wc3 = Y.wc2; Y.ws3 = Y.ws2;
+                        Y.wc2 = Y.wc1; Y.ws2 = Y.ws1; Y.wc1 = vx.x; Y.ws1 = vx.y;
+                    }
+                    Y.m3 = Y.m2; Y.s3 = Y.s2;
+                    Y.m2 = Y.m1; Y.s2 = Y.s1;
+                    Y.m1 = m0;   Y.s1 = s0;
+                    Y.vc4 = Y.vc3; Y.vs4 = Y.vs3; Y.vc3 = Y.vc2; Y.vs3 = Y.vs2;
+                    Y.vc2 = Y.vc1; Y.vs2 = Y.vs1; Y.vc1 = vy.x; Y.vs1 = vy.y;
+                    if (FINAL && u == NY - 1) {
+                        const int rout = rout0 + ir;
+                        if (col_ok && rout >= yb && rout < ye) {
+                            const size_t o = size_t(rout) * Nx;
+                            qo_h[o] = h;
+                            qo_px[o] = px;
+                            qo_py[o] = p;
+                        }
+                    } else {
+                        T *out = const_cast<T *>(st_base[u]) + LVL + hout;  // level j+1, other half
+                        out[(0 * R + ir) * W_IN] = h;
+                        out[(1 * R + ir) * W_IN] = px;
+                        out[(2 * R + ir) * W_IN] = p;
                     }
                 }
             }
-        }
+        };
+        if (last_is_final) rows(std::integral_constant<bool, true>());
+        else rows(std::integral_constant<bool, false>());
+        itcur = it + 1;
+        r0w = wrap_down(r0w + R, Ny);
         cp_async_wait_all();
         __syncthreads();
     }
 }
 
-template <typename T, int K, int NY, int R>
+template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
+__global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB) sweep_kernel(const SweepParams prm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (prm.a.fam0 + int(blockIdx.z) == 0) sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, smem_raw);
+    else sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, smem_raw);
+}
+
+template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 int occupancy_t() {
-    using Cfg = SweepCfg<T, K, NY, R>;
-    cudaFuncSetAttribute(sweep_kernel<T, K, NY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::SMEM));
+    using Cfg = SweepCfg<T, K, R, NY>;
+    using L = SweepLayout<T, K, R, INTER>;
+    cudaFuncSetAttribute(sweep_kernel<T, K, R, NY, INTER, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(L::SMEM));
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, K, NY, R>, Cfg::NT, Cfg::SMEM) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, K, R, NY, INTER, UNIT>, Cfg::NT,
+                                                      L::SMEM) != cudaSuccess)
         n = 1;
     cudaGetLastError();
     return n < 1 ? 1 : n;
 }
 
-template <typename T, int K, int NY, int R>
+template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
-    using Cfg = SweepCfg<T, K, NY, R>;
+    using Cfg = SweepCfg<T, K, R, NY>;
+    using L = SweepLayout<T, K, R, INTER>;
     static int configured_dev = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_dev != dev) {
-        e = cudaFuncSetAttribute(sweep_kernel<T, K, NY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(Cfg::SMEM));
+        e = cudaFuncSetAttribute(sweep_kernel<T, K, R, NY, INTER, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(L::SMEM));
         if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
     SweepParams prm;
     prm.a = a;
-    // TM: hub q2, x-partner q4, y-partner q3.
-    //   C_X on (q2,q4): q2' = c q2 - s q4 -> orientation -1; V_X row q4 <- -sin b2 q2 (partner, -1)
-    //   C_Y on (q2,q3): q2' = c q2 + s q3 -> orientation +1; V_Y row q3 <- +sin b3 q2 (partner, +1)
-    prm.fam[0] = Family{2, 4, 3, C_TM_M, C_TM_S, C_TM_M, C_TM_S, C_TM_VXS, C_TM_VXC, C_TM_VYS, C_TM_VYC,
-                        -1.f, +1.f, -1.f, +1.f, 0, 0};
-    // TE: hub q5, x-partner q1, y-partner q0.
-    //   C_X on (q1,q5): q5' = s q1 + c q5 -> orientation +1; V_X row q5 <- +sin b0 q1 (hub, +1)
-    //   C_Y on (q0,q5): q5' = -s q0 + c q5 -> orientation -1; V_Y row q5 <- -sin b1 q0 (hub, -1)
-    prm.fam[1] = Family{5, 1, 0, C_TE_XM, C_TE_XS, C_TE_YM, C_TE_YS, C_TE_VXS, C_TE_VXC, C_TE_VYS, C_TE_VYC,
-                        +1.f, -1.f, +1.f, -1.f, 1, 1};
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
     dim3 grid(nsx, ncy, nfam);
-    sweep_kernel<T, K, NY, R><<<grid, Cfg::NT, Cfg::SMEM, st>>>(prm);
+    sweep_kernel<T, K, R, NY, INTER, UNIT><<<grid, Cfg::NT, L::SMEM, st>>>(prm);
     return cudaGetLastError();
+}
+
+// Dispatch on the step order and the potential variant.
+template <typename T, int K, int R, int NY>
+cudaError_t launch_sweep_modes(const SweepArgs &a, int nfam, cudaStream_t st) {
+    if (a.interleaved) {
+        return a.unitary ? launch_sweep_t<T, K, R, NY, true, true>(a, nfam, st)
+                         : launch_sweep_t<T, K, R, NY, true, false>(a, nfam, st);
+    }
+    return a.unitary ? launch_sweep_t<T, K, R, NY, false, true>(a, nfam, st)
+                     : launch_sweep_t<T, K, R, NY, false, false>(a, nfam, st);
+}
+
+template <typename T, int K, int R, int NY>
+int occupancy_modes(int interleaved) {
+    return interleaved ? occupancy_t<T, K, R, NY, true, false>() : occupancy_t<T, K, R, NY, false, false>();
 }
 
 }  // namespace qla

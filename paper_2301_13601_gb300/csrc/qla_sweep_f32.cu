@@ -3,29 +3,31 @@
 
 namespace qla {
 
+// (K, rows per iteration R, column pipelines per thread NY): shared memory is
+// 112 KB for K = 1, 2 (two CTAs per SM) and 224 KB for K = 4.
 cudaError_t launch_sweep_f32(int K, const SweepArgs &a, int nfam, cudaStream_t st) {
     switch (K) {
-        case 1: return launch_sweep_t<float, 1, 1, 8>(a, nfam, st);
-        case 2: return launch_sweep_t<float, 2, 1, 8>(a, nfam, st);
-        case 4: return launch_sweep_t<float, 4, 2, 8>(a, nfam, st);
+        case 1: return launch_sweep_modes<float, 1, 8, 1>(a, nfam, st);
+        case 2: return launch_sweep_modes<float, 2, 4, 2>(a, nfam, st);
+        case 4: return launch_sweep_modes<float, 4, 4, 2>(a, nfam, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 int sweep_strip_width() { return W_IN; }
 
-int sweep_occupancy_f32(int K) {
-    switch (K) {
-        case 1: return occupancy_t<float, 1, 1, 8>();
-        case 2: return occupancy_t<float, 2, 1, 8>();
-        case 4: return occupancy_t<float, 4, 2, 8>();
-        default: return 1;
-    }
-}
-
 bool sweep_supported(int precision, int K) {
     if (precision == 0) return K == 1 || K == 2 || K == 4;
     return K == 1 || K == 2;
+}
+
+int sweep_occupancy_f32(int K, int interleaved) {
+    switch (K) {
+        case 1: return occupancy_modes<float, 1, 8, 1>(interleaved);
+        case 2: return occupancy_modes<float, 2, 4, 2>(interleaved);
+        case 4: return occupancy_modes<float, 4, 4, 2>(interleaved);
+        default: return 1;
+    }
 }
 
 }  // namespace qla
