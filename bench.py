@@ -298,6 +298,44 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """64 lattices of uneven sizes in one persistent graph launch per bench step."""
+    import torch
+
+    from paper_2301_13601_gb300 import build as _build
+    from paper_2301_13601_gb300 import media
+    from paper_2301_13601_gb300.qla import Batch
+
+    _build.build()
+    ws = media.workload_batch64()
+    K = args.steps_per_pass or 4
+    inst = []
+    for w in ws:
+        steps = max(K, (w.steps // args.batch_step_scale) // K * K)
+        inst.append({"n": w.medium(), "delta": w.delta, "nsteps": steps,
+                     "pulse": ("Ez" if w.pulse.pol == media.POL_EZ else "Ey", w.pulse.x0, w.pulse.sigma, 1.0),
+                     "chunk_rows": args.chunk_rows})
+    with Batch(inst, steps_per_pass=K) as b:
+        info = b.info()
+        for _ in range(args.warmup):
+            b.run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b.run()
+        el = time.perf_counter() - t0
+    value = info["site_updates"] * args.steps / el
+    peak, peak_kind = measured_peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "lattices": len(inst), "sides": sorted({w.Nx for w in ws}),
+                       "qla_steps_per_lattice": f"{min(i['nsteps'] for i in inst)}-{max(i['nsteps'] for i in inst)}",
+                       "steps_per_pass": K, "work_items": info["work_items"], "launch": "one persistent kernel in a CUDA graph"},
+            "bandwidth_equivalent_frac": value * BYTES_PER_SITE_UPDATE / 1e9 / peak, "peak_kind": peak_kind}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,7 +344,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["cylinders8192", "ellipse2048", "cylinder256"], default="cylinders8192")
+    ap.add_argument("--workload", choices=["cylinders8192", "ellipse2048", "cylinder256", "batch64"],
+                    default="cylinders8192")
+    ap.add_argument("--batch-step-scale", type=int, default=10, help="batch64: steps of each lattice divided by this")
     ap.add_argument("--chunk-rows", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="no e2e leg and no CPU baseline (profiling runs)")
     args = ap.parse_args()
@@ -314,6 +354,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -207,6 +207,57 @@ const char *qla_status_string(qla_status s);
 /* Release the context and any device memory it allocated. NULL is a no-op. */
 void qla_destroy(qla_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched lattices: many independent scattering problems (each its own
+ * periodic lattice, medium, delta and pulse, Sec. 4 setting) advanced by one
+ * persistent kernel launch that is captured once into a CUDA graph and
+ * replayed by every qla_batch_run. The kernel takes work items
+ * (instance, pass of steps_per_pass fused steps, family, tile) from a queue
+ * ordered by pass; before a pass it waits, with a time limit, for the
+ * previous pass of the same lattice to complete. FP32 only.
+ * ------------------------------------------------------------------------- */
+typedef struct qla_batch qla_batch;
+
+typedef struct {
+    int Nx, Ny;                      /* lattice; Nx a multiple of 4, Nx*Ny <= 2^31 - 1 */
+    const double *n_x, *n_y, *n_z;   /* host [Ny][Nx] refractive indices, copied */
+    double delta;                    /* 0 < delta <= 0.5 (Eq. 24-25) */
+    long long nsteps;                /* steps per qla_batch_run; a multiple of steps_per_pass */
+    int pulse_polarization;          /* QLA_POL_EZ or QLA_POL_EY: initial pulse as qla_init_pulse; -1: zero state */
+    double pulse_x0, pulse_sigma, pulse_amplitude;
+    int chunk_rows;                  /* rows per tile; 0 = automatic */
+} qla_instance_desc;
+
+/* Create a batch of `count` lattices (descs copied; the host arrays are only
+ * read during the call). opt: precision must be QLA_FP32; steps_per_pass 2 or 4
+ * (0 = 4); sequence and potential apply to every lattice; opt->stream is
+ * ignored (the batch owns a stream). Errors: QLA_EINVAL (bad descriptor),
+ * QLA_EUNSUPPORTED (precision or steps_per_pass), QLA_ENOMEM, QLA_ECUDA. */
+qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla_options *opt, qla_batch **out);
+
+/* Advance every lattice by its nsteps (one graph launch; blocks until done).
+ * QLA_ETIMEOUT if a dependency wait exceeded its limit (the states are then
+ * partially advanced and should be discarded). */
+qla_status qla_batch_run(qla_batch *b);
+
+/* State of lattice i (creation order) as a host float array [6][Ny][Nx]. */
+qla_status qla_batch_get_fields_f32(qla_batch *b, int i, float *q);
+
+/* Diagnostics of lattice i (as qla_diagnostics). */
+qla_status qla_batch_diagnostics(qla_batch *b, int i, qla_diag *out);
+
+/* Work items per run, steps per pass, and site-updates per run. */
+qla_status qla_batch_info(const qla_batch *b, long long *total_items, int *steps_per_pass, long long *site_updates);
+
+/* Test hook: limit of each dependency wait in nanoseconds (default 4 s), and a
+ * number of extra tile completions every dependency waits for (0 normally; a
+ * positive value makes the first wait run out, which must end the run with
+ * QLA_ETIMEOUT instead of hanging). Takes effect at the next qla_batch_run. */
+qla_status qla_batch_set_wait_limit(qla_batch *b, long long timeout_ns, int withhold);
+
+const char *qla_batch_last_error(const qla_batch *b);
+void qla_batch_destroy(qla_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

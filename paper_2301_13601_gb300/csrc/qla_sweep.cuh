@@ -305,7 +305,7 @@ struct YPipe {
 };
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
-__device__ __forceinline__ void sweep_body(const SweepArgs &A, unsigned char *smem_raw) {
+__device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int chunk_idx, unsigned char *smem_raw) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     using T2 = typename Ar<T>::T2;
@@ -329,11 +329,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, unsigned char *sm
     const int lane = tid & 31;
     const int warp = tid >> 5;
 
-    const int xs0 = blockIdx.x * A.w_valid;   // first output column of the strip
+    const int xs0 = strip * A.w_valid;   // first output column of the strip
     const int xbase = xs0 - 4 * K;            // global column of strip column 0 (may be < 0)
     const int xb = wrapi(xbase, Nx);
     const bool nowrap = xbase >= 0 && xbase + W_IN <= Nx;
-    const int yb = blockIdx.y * A.chunk;
+    const int yb = chunk_idx * A.chunk;
     const int ye = min(yb + A.chunk, Ny);
     const int F0 = yb - 4 * K;                // first row fed to level 0
     const int nit = (ye - yb + 8 * K + R - 1) / R + K - 1;
@@ -612,8 +612,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, unsigned char *sm
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB) sweep_kernel(const SweepParams prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (prm.a.fam0 + int(blockIdx.z) == 0) sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, smem_raw);
-    else sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, smem_raw);
+    if (prm.a.fam0 + int(blockIdx.z) == 0) sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw);
+    else sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>

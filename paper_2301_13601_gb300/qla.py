@@ -31,6 +31,8 @@ EXPORTS = [
     "qla_set_fields_f32", "qla_step", "qla_energy", "qla_divB", "qla_diagnostics", "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
     "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc",
+    "qla_batch_create", "qla_batch_run", "qla_batch_get_fields_f32", "qla_batch_diagnostics", "qla_batch_info",
+    "qla_batch_set_wait_limit", "qla_batch_last_error", "qla_batch_destroy",
 ]
 
 
@@ -294,6 +296,136 @@ class Simulation:
         if self._ctx is not None:
             self._L.qla_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("n_x", ctypes.POINTER(ctypes.c_double)),
+                ("n_y", ctypes.POINTER(ctypes.c_double)), ("n_z", ctypes.POINTER(ctypes.c_double)),
+                ("delta", ctypes.c_double), ("nsteps", ctypes.c_longlong), ("pulse_polarization", ctypes.c_int),
+                ("pulse_x0", ctypes.c_double), ("pulse_sigma", ctypes.c_double),
+                ("pulse_amplitude", ctypes.c_double), ("chunk_rows", ctypes.c_int)]
+
+
+def _batch_sigs(L):
+    P = ctypes.POINTER
+    v, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    L.qla_batch_create.argtypes = [i, P(InstanceDesc), P(Options), P(v)]
+    L.qla_batch_create.restype = st
+    L.qla_batch_run.argtypes = [v]
+    L.qla_batch_run.restype = st
+    L.qla_batch_get_fields_f32.argtypes = [v, i, P(ctypes.c_float)]
+    L.qla_batch_get_fields_f32.restype = st
+    L.qla_batch_diagnostics.argtypes = [v, i, P(Diag)]
+    L.qla_batch_diagnostics.restype = st
+    L.qla_batch_info.argtypes = [v, P(ctypes.c_longlong), P(i), P(ctypes.c_longlong)]
+    L.qla_batch_info.restype = st
+    L.qla_batch_set_wait_limit.argtypes = [v, ctypes.c_longlong, i]
+    L.qla_batch_set_wait_limit.restype = st
+    L.qla_batch_last_error.argtypes = [v]
+    L.qla_batch_last_error.restype = ctypes.c_char_p
+    L.qla_batch_destroy.argtypes = [v]
+    L.qla_batch_destroy.restype = None
+
+
+class Batch:
+    """Many independent lattices advanced by one persistent graph launch (FP32).
+
+    instances: list of dicts with keys n (tuple of three (Ny, Nx) arrays), delta,
+    nsteps, and optionally pulse=(polarization 'Ez'/'Ey', x0, sigma, amplitude)
+    and chunk_rows.
+    """
+
+    def __init__(self, instances, steps_per_pass: int = 4, sequence="interleaved", potential="paper",
+                 device: Optional[int] = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqla needs a CUDA GPU; no CPU fallback exists")
+        L = load_library()
+        _batch_sigs(L)
+        self._L = L
+        self._b = None
+        self._keep = []
+        descs = (InstanceDesc * len(instances))()
+        self.shapes = []
+        for k, ins in enumerate(instances):
+            n = [np.ascontiguousarray(a, dtype=np.float64) for a in ins["n"]]
+            self._keep.append(n)
+            Ny, Nx = n[0].shape
+            self.shapes.append((6, Ny, Nx))
+            d = descs[k]
+            d.Nx, d.Ny = Nx, Ny
+            d.n_x, d.n_y, d.n_z = (_dptr(a) for a in n)
+            d.delta = float(ins["delta"])
+            d.nsteps = int(ins["nsteps"])
+            pulse = ins.get("pulse")
+            if pulse is None:
+                d.pulse_polarization = -1
+            else:
+                d.pulse_polarization = _code("polarization", {"Ez": POL_EZ, "Ey": POL_EY}, pulse[0])
+                d.pulse_x0, d.pulse_sigma, d.pulse_amplitude = float(pulse[1]), float(pulse[2]), float(pulse[3])
+            d.chunk_rows = int(ins.get("chunk_rows", 0))
+        opt = Options()
+        L.qla_default_options(ctypes.byref(opt))
+        opt.steps_per_pass = int(steps_per_pass)
+        opt.sequence = _code("sequence", {"interleaved": SEQ_INTERLEAVED, "plain": SEQ_PLAIN}, sequence)
+        opt.potential = _code("potential", {"paper": POT_PAPER, "unitary": POT_UNITARY}, potential)
+        opt.device = torch.cuda.current_device() if device is None else int(device)
+        b = ctypes.c_void_p()
+        st = L.qla_batch_create(len(instances), descs, ctypes.byref(opt), ctypes.byref(b))
+        if st != 0:
+            raise QLAError(st, "qla_batch_create")
+        self._b = b
+
+    def run(self):
+        st = self._L.qla_batch_run(self._b)
+        if st != 0:
+            raise QLAError(st, "qla_batch_run", (self._L.qla_batch_last_error(self._b) or b"").decode())
+
+    def run_status(self) -> int:
+        return int(self._L.qla_batch_run(self._b))
+
+    def set_wait_limit(self, timeout_ns: int, withhold: int = 0):
+        st = self._L.qla_batch_set_wait_limit(self._b, int(timeout_ns), int(withhold))
+        if st != 0:
+            raise QLAError(st, "qla_batch_set_wait_limit")
+
+    def get_fields(self, i: int) -> np.ndarray:
+        out = np.empty(self.shapes[i], dtype=np.float32)
+        st = self._L.qla_batch_get_fields_f32(self._b, int(i), _fptr(out))
+        if st != 0:
+            raise QLAError(st, "qla_batch_get_fields_f32")
+        return out
+
+    def diagnostics(self, i: int) -> dict:
+        d = Diag()
+        st = self._L.qla_batch_diagnostics(self._b, int(i), ctypes.byref(d))
+        if st not in (0, 5):
+            raise QLAError(st, "qla_batch_diagnostics")
+        return {"energy": d.energy, "div_l2_sq": d.div_l2_sq, "div_max": d.div_max, "b_max": d.b_max,
+                "nonfinite": d.nonfinite}
+
+    def info(self):
+        t, k, s = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong()
+        self._L.qla_batch_info(self._b, ctypes.byref(t), ctypes.byref(k), ctypes.byref(s))
+        return {"work_items": t.value, "steps_per_pass": k.value, "site_updates": s.value}
+
+    def close(self):
+        if self._b is not None:
+            self._L.qla_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:
