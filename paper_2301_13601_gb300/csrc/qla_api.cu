@@ -461,3 +461,24 @@ void qla_destroy(qla_ctx *c) {
 }
 
 }  // extern "C"
+
+namespace qla {
+
+bool ctx_view(qla_ctx *c, CtxView *v) {
+    if (!c || !v) return false;
+    v->Nx = c->Nx;
+    v->Ny = c->Ny;
+    v->precision = c->opt.precision;
+    v->stream = c->stream;
+    v->cur_state = c->state[c->cur];
+    v->spare_state = c->state[c->cur ^ 1];
+    v->has_state = c->has_state ? 1 : 0;
+    return true;
+}
+
+void ctx_commit_spare(qla_ctx *c, long long steps) {
+    c->cur ^= 1;
+    c->steps += steps;
+}
+
+}  // namespace qla

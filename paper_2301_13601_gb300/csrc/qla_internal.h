@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/qla.h"
+
 namespace qla {
 
 // Coefficient pair planes: NPAIR planes of [Ny][Nx] pairs (x = cos(a) - 1,
@@ -83,4 +85,48 @@ size_t diag_scratch_bytes(int Nx, int Ny);
 cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, void *scratch,
                                DiagResult *out_dev, cudaStream_t st);
 
+
+// ---------------------------------------------------------------------------
+// Surrogate building blocks (BF16 tensor-core convolution and friends).
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+    const void *x;        // BF16 [nimg][H][W][cin]
+    const void *w;        // BF16 packed [9][cin/8][nout][8]
+    const float *bias;    // [nout] or null
+    int nimg, H, W;       // images of H x W (each periodic)
+    int epi;              // QLA_EPI_*
+    const void *aux0;     // GELU: BF16 residual or null; DGRAD: FP32 g_in or null; QUPDATE: FP32 q_in [nimg][6][H][W]
+    const void *zprev;    // DGRAD: BF16 pre-activation [nimg][H][W][nout]
+    void *out0;           // GELU: BF16 z or null; LINEAR: FP32; DGRAD: FP32 g; QUPDATE: FP32 q_out [nimg][6][H][W]
+    void *out1;           // GELU: BF16 activation; DGRAD: BF16 dz
+    float scale;          // QUPDATE
+    int *error;           // set to 1 when a bounded wait runs out
+};
+// Supported (cin, nout): (16, 64), (64, 64), (64, 16).
+bool conv_supported(int cin, int nout);
+cudaError_t launch_conv(int cin, int nout, const ConvArgs &a, cudaStream_t st);
+
+// Weight packing modes: plain, adjoint (transpose + 180-degree flip), and
+// plain with the input channels of the surrogate's first layer
+// (packed c: 0-5 -> logical c, 6-11 -> logical c-6, 12-14 -> logical c-6, 15 -> 0).
+enum PackMode { PACK_PLAIN = 0, PACK_ADJOINT = 1, PACK_TIED_INPUT = 2 };
+cudaError_t launch_pack_weights(const float *w, int nout, int cin, int nout_pad, int cin_pad, int mode,
+                                void *packed, cudaStream_t st);
+
 }  // namespace qla
+
+// Access to a QLA context from other parts of the library (the surrogate
+// rollout advances a context's state and hands steps back to it).
+namespace qla {
+struct CtxView {
+    int Nx, Ny, precision;
+    cudaStream_t stream;
+    void *cur_state;     // current state [6][Ny][Nx]
+    void *spare_state;   // the other state buffer (free between steps)
+    int has_state;
+};
+bool ctx_view(qla_ctx *c, CtxView *v);
+// The spare buffer, now holding the state `steps` steps later, becomes current.
+void ctx_commit_spare(qla_ctx *c, long long steps);
+}  // namespace qla
+

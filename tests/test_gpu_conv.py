@@ -144,3 +144,94 @@ def test_conv_rejects_bad_arguments():
     x = torch.zeros((2, 128, 32), dtype=torch.bfloat16, device=dev)  # unsupported channel count
     with pytest.raises(QLAError):
         S.conv3x3(x, w, 64, S.EPI_LINEAR, out, error_flag=err)
+
+
+def test_images_wrap_on_their_own():
+    """nimg stacked images: each is periodic by itself (no leakage between images)."""
+    nimg, H, W, cin, nout = 3, 2, 128, 64, 16
+    rng = np.random.default_rng(51)
+    x = bf16_round(rng.standard_normal((nimg, H, W, cin)))
+    w = rng.standard_normal((nout, cin, 3, 3)) / np.sqrt(9 * cin)
+    wq = bf16_round(w)
+    b = rng.standard_normal(nout) * 0.1
+    q = rng.standard_normal((nimg, 6, H, W)).astype(np.float32)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = torch.empty((nimg, H, W, nout), dtype=torch.float32, device=dev)
+    xd = to_dev(x, torch.bfloat16)
+    wp = packed(w, cin, nout)
+    S.conv3x3(xd, wp, nout, S.EPI_LINEAR, out, bias=to_dev(b, torch.float32), error_flag=err)
+    qo = torch.empty((nimg, 6, H, W), dtype=torch.float32, device=dev)
+    S.conv3x3(xd, wp, nout, S.EPI_QUPDATE, qo, bias=to_dev(b, torch.float32), aux0=to_dev(q, torch.float32),
+              scale=0.5, error_flag=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    got = out.cpu().numpy()
+    for i in range(nimg):
+        ref = cnn.conv3x3(x[i], wq, b)
+        assert np.max(np.abs(got[i] - ref)) <= 2e-5 * np.max(np.abs(ref))
+        refq = q[i] + 0.5 * np.moveaxis(ref[:, :, :6], 2, 0)
+        assert np.max(np.abs(qo[i].cpu().numpy() - refq)) <= 1e-5 * np.abs(refq).max()
+
+
+def test_gelu_without_z_store():
+    H, W, cin, nout = 2, 128, 16, 64
+    x, w, wq, b = make_case(H, W, cin, nout, seed=61)
+    act = cnn.gelu(cnn.conv3x3(x, wq, b))
+    ao = torch.empty((H, W, nout), dtype=torch.bfloat16, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    S.conv3x3(to_dev(x, torch.bfloat16), packed(w, cin, nout), nout, S.EPI_GELU, None, ao,
+              bias=to_dev(b, torch.float32), error_flag=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert np.max(np.abs(ao.float().cpu().numpy() - act)) < 2 ** -8 * 1.5 * (np.abs(act).max() + 1.0)
+
+
+@pytest.mark.parametrize("cin,nout", [(64, 64), (16, 64)])
+def test_long_row_segments(cin, nout):
+    """Many rows per CTA: the rolling window crosses column blocks and images."""
+    nimg, H, W = 2, 700, 256
+    rng = np.random.default_rng(71)
+    x = bf16_round(rng.standard_normal((nimg, H, W, cin)))
+    w = rng.standard_normal((nout, cin, 3, 3)) / np.sqrt(9 * cin)
+    wq = bf16_round(w)
+    b = rng.standard_normal(nout) * 0.1
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = torch.empty((nimg, H, W, nout), dtype=torch.float32, device=dev)
+    S.conv3x3(to_dev(x, torch.bfloat16), packed(w, cin, nout), nout, S.EPI_LINEAR, out,
+              bias=to_dev(b, torch.float32), error_flag=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    got = out.cpu().numpy()
+    for i in range(nimg):
+        ref = cnn.conv3x3(x[i], wq, b)
+        assert np.max(np.abs(got[i] - ref)) <= 2e-5 * np.max(np.abs(ref))
+
+
+def test_residual_from_global_memory():
+    """EPI_GELU with a residual tensor other than the input (read from global memory)."""
+    H, W, c = 3, 128, 64
+    x, w, wq, b = make_case(H, W, c, c, seed=81)
+    res = bf16_round(np.random.default_rng(82).standard_normal((H, W, c)))
+    act = cnn.gelu(cnn.conv3x3(x, wq, b)) + res
+    ao = torch.empty((H, W, c), dtype=torch.bfloat16, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    S.conv3x3(to_dev(x, torch.bfloat16), packed(w, c, c), c, S.EPI_GELU, None, ao, bias=to_dev(b, torch.float32),
+              aux0=to_dev(res, torch.bfloat16), error_flag=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert np.max(np.abs(ao.float().cpu().numpy() - act)) < 2 ** -8 * 1.5 * (np.abs(act).max() + 1.0)
+
+
+def test_residual_from_staged_input():
+    """EPI_GELU with the residual equal to the input: read from the staged rows."""
+    H, W, c = 5, 256, 64
+    x, w, wq, b = make_case(H, W, c, c, seed=91)
+    act = cnn.gelu(cnn.conv3x3(x, wq, b)) + x
+    xd = to_dev(x, torch.bfloat16)
+    zo = torch.empty((H, W, c), dtype=torch.bfloat16, device=dev)
+    ao = torch.empty_like(zo)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    S.conv3x3(xd, packed(w, c, c), c, S.EPI_GELU, zo, ao, bias=to_dev(b, torch.float32), aux0=xd, error_flag=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert np.max(np.abs(ao.float().cpu().numpy() - act)) < 2 ** -8 * 1.5 * (np.abs(act).max() + 1.0)

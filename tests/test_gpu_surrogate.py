@@ -1,0 +1,176 @@
+"""The surrogate network on the GPU against the FP64 numpy reference (oracle/cnn.py).
+
+The GPU path computes with BF16 weights and activations and FP32
+accumulation; the reference runs in FP64 on the same BF16-rounded weights and
+BF16-rounded n. Each BF16 rounding is relative 2^-9 (RMS well below); the
+forward chain holds about 10 such roundings (z and a of five layers) and the
+backward about as many again (g, dz), so the derived tolerance is
+sqrt(20) x 2^-9 x 3 (an amplification margin) ~ 3e-2 on relative L2 errors.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn
+from paper_2301_13601_gb300 import surrogate as S
+
+pytestmark = pytest.mark.gpu
+dev = "cuda"
+TOL = 3e-2
+
+
+def bf16(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(S.param_count(), dtype=np.float32)
+    for l, (ws, shape, bs) in enumerate(S.param_slices()):
+        cin = shape[1]
+        p[ws] = rng.standard_normal(np.prod(shape)) * np.sqrt(2.0 / (9 * cin)) * (0.5 if l == 5 else 1.0)
+        p[bs] = rng.standard_normal(shape[0]) * 0.05
+    return p
+
+
+def oracle_weights(p):
+    ws, bs = [], []
+    for (wsl, shape, bsl) in S.param_slices():
+        ws.append(bf16(p[wsl]).reshape(shape))
+        bs.append(p[bsl].astype(np.float64))
+    return ws, bs
+
+
+def make_inputs(nimg, H, W, seed):
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal((nimg, 6, H, W)).astype(np.float32)
+    n = rng.uniform(1.0, 3.0, size=(nimg, 3, H, W)).astype(np.float32)
+    return q, n
+
+
+def oracle_x0(q, n, i):
+    return np.concatenate([np.moveaxis(q[i].astype(np.float64), 0, 2), np.moveaxis(bf16(n[i]), 0, 2)], axis=2)
+
+
+SCALE = 1.0 / 16
+
+
+def test_param_layout():
+    assert S.param_count() == sum(c * o * 9 + o for c, o in S.LAYERS) == 156422
+
+
+def test_forward_matches_oracle():
+    nimg, H, W = 2, 4, 128
+    p = random_params(1)
+    q, n = make_inputs(nimg, H, W, 2)
+    with S.Surrogate(H, W, nimg=nimg, out_scale=SCALE) as sur:
+        sur.set_params(p)
+        qi = torch.as_tensor(q, device=dev)
+        qo = torch.empty_like(qi)
+        sur.forward(qi, torch.as_tensor(n, device=dev), qo)
+        sur.synchronize()
+        dq = (qo.cpu().numpy().astype(np.float64) - q)
+    ws, bs = oracle_weights(p)
+    for i in range(nimg):
+        ref, _ = cnn.forward(oracle_x0(q, n, i), ws, bs, SCALE)
+        ref = np.moveaxis(ref, 2, 0)
+        assert np.linalg.norm(dq[i] - ref) / np.linalg.norm(ref) < TOL
+
+
+def run_grad(p, q, n, qt):
+    nimg, _, H, W = q.shape
+    with S.Surrogate(H, W, nimg=nimg, out_scale=SCALE, train=True) as sur:
+        sur.set_params(p)
+        loss, g = sur.loss_grad(torch.as_tensor(q, device=dev), torch.as_tensor(n, device=dev),
+                                torch.as_tensor(qt, device=dev), want_loss=True, want_grad=True)
+    return loss, g
+
+
+def test_gradients_match_oracle():
+    nimg, H, W = 2, 8, 128
+    p = random_params(3)
+    q, n = make_inputs(nimg, H, W, 4)
+    rng = np.random.default_rng(5)
+    qt = (q + 0.05 * rng.standard_normal(q.shape)).astype(np.float32)
+    loss, g = run_grad(p, q, n, qt)
+    ws, bs = oracle_weights(p)
+    outs, caches = [], []
+    for i in range(nimg):
+        o, c = cnn.forward(oracle_x0(q, n, i), ws, bs, SCALE)
+        outs.append(o)
+        caches.append(c)
+    delta = [np.moveaxis(qt[i].astype(np.float64) - q[i], 0, 2) for i in range(nimg)]
+    den = sum(np.sum(d * d) for d in delta)
+    ref_loss = sum(np.sum((outs[i] - delta[i]) ** 2) for i in range(nimg)) / den
+    assert abs(loss / ref_loss - 1.0) < TOL
+    gref = np.zeros_like(g, dtype=np.float64)
+    for i in range(nimg):
+        dW, dB = cnn.backward(2.0 * (outs[i] - delta[i]) / den, ws, caches[i], SCALE)
+        for l, (wsl, shape, bsl) in enumerate(S.param_slices()):
+            gref[wsl] += dW[l].ravel()
+            gref[bsl] += dB[l]
+    for l, (wsl, shape, bsl) in enumerate(S.param_slices()):
+        for sl in (wsl, bsl):
+            err = np.linalg.norm(g[sl] - gref[sl]) / np.linalg.norm(gref[sl])
+            assert err < TOL, (l, sl, err)
+    cos = g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref))
+    assert cos > 0.999
+
+
+def test_gradients_are_deterministic():
+    p = random_params(6)
+    q, n = make_inputs(2, 4, 256, 7)
+    qt = (q * 1.01).astype(np.float32)
+    l1, g1 = run_grad(p, q, n, qt)
+    l2, g2 = run_grad(p, q, n, qt)
+    assert l1 == l2 and np.array_equal(g1, g2)
+
+
+def test_training_reduces_loss_on_a_learnable_map():
+    """Target: Q + 0.1 (shift of Q by one cell in x - Q), a linear stencil the network can represent."""
+    nimg, H, W = 2, 16, 128
+    q, n = make_inputs(nimg, H, W, 8)
+    qt = (q + 0.1 * (np.roll(q, 1, axis=3) - q)).astype(np.float32)
+    with S.Surrogate(H, W, nimg=nimg, out_scale=SCALE, train=True, seed=9) as sur:
+        qi, ni, ti = (torch.as_tensor(a, device=dev) for a in (q, n, qt))
+        first = sur.train_step(qi, ni, ti, 0.0, want_loss=True)
+        for it in range(300):
+            sur.train_step(qi, ni, ti, 2e-3)
+        last, _ = sur.loss_grad(qi, ni, ti)
+    assert first > 0.5
+    assert last < 0.1 * first
+
+
+def test_rollout_falls_back_to_plain_qla():
+    """drift_tol = 0 rejects every proposal: the result is plain QLA, bit for bit."""
+    from paper_2301_13601_gb300 import media
+    from paper_2301_13601_gb300.qla import Simulation
+
+    Nx, Ny = 128, 64
+    nfield = media.medium(Nx, Ny, [media.Ellipse(70, 30, 20, 12, 0.3, (1.5, 2.0, 2.5), 3.0)])
+    nf = torch.as_tensor(np.stack(nfield), dtype=torch.float32, device=dev)
+    with S.Surrogate(Ny, Nx, K=16, seed=10) as sur, Simulation(*nfield, 0.05) as a, Simulation(*nfield, 0.05) as b:
+        a.init_pulse("Ez", 40, 10)
+        b.init_pulse("Ez", 40, 10)
+        st = sur.rollout(a, nf, 3, drift_tol=0.0)
+        b.step(48)
+        assert st["fallback_calls"] == 3 and st["surrogate_calls"] == 0
+        assert np.array_equal(a.get_fields(np.float32), b.get_fields(np.float32))
+        assert a.step_count == 48
+        st = sur.rollout(a, nf, 2, drift_tol=1e30)
+        assert st["surrogate_calls"] == 2 and a.step_count == 80
+
+
+def test_surrogate_rejects_bad_arguments():
+    from paper_2301_13601_gb300.qla import QLAError
+
+    with pytest.raises(QLAError):
+        S.Surrogate(64, 100)  # W not a multiple of 128
+    with S.Surrogate(8, 128) as sur:  # no training buffers
+        q = torch.zeros((1, 6, 8, 128), device=dev)
+        with pytest.raises(QLAError):
+            sur.loss_grad(q, torch.ones((1, 3, 8, 128), device=dev), q)
+        bad = np.zeros(S.param_count(), dtype=np.float32)
+        bad[5] = np.nan
+        with pytest.raises(QLAError):
+            sur.set_params(bad)
