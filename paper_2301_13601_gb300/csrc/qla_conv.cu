@@ -67,7 +67,7 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
 template <int CCH, int NOUT>
 struct ConvLayout {
     static constexpr int HALO_PX = 130;
-    static constexpr int NS = 5;  // rows y-1..y+1 for the MMA of row y, y+2 waiting, y+3 loading
+    static constexpr int NS = CCH >= 8 ? 6 : 8;  // MMA needs 3 rows; the loader runs up to NS-3 rows ahead
     static constexpr int A_BYTES = CCH * NS * HALO_PX * 16;
     static constexpr int B_BYTES = 9 * CCH * NOUT * 16;
     static constexpr int A_OFF = 0;
@@ -77,25 +77,63 @@ struct ConvLayout {
     static constexpr int TMEM_COLS = 2 * ACC_COLS;          // two accumulators
 };
 
-// Persistent conv kernel. Work = rows of 128-pixel column blocks, ordered
-// (image, column block, row); each CTA takes a contiguous range and walks down
-// its column blocks with a rolling window of halo rows, so every input row is
-// loaded once per block. Per output row y (256 threads = 8 warps):
-//   a) cp.async row y+3 into the ring (its slot was last read by the MMA of y-1)
-//   b) wait for row y+2, fence, barrier
-//   c) one thread issues the 9 x CCH/2 MMAs of row y+1 into the other accumulator
-//   d) all wait for the MMAs of row y, then run the fused epilogue of row y
-// so loads, tensor-core work and epilogue of three rows overlap.
-// Epilogue: warp w reads TMEM lanes 32 (w % 4)... (its pixels) and the column
-// half w / 4 (32 channels); for NOUT = 16 only warps 0-3 work.
+constexpr int CONV_EPI_WARPS = 8;
+constexpr int CONV_MMA_WARP = 8;
+constexpr int CONV_LOAD_WARP = 9;
+constexpr int CONV_THREADS = 320;
+constexpr uint32_t CONV_WAIT_TRIES = 1u << 22;
+
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(tc::smem_addr(bar))
+                 : "memory");
+}
+
+// Segment walker shared by all roles: the CTA's rows, ordered (image, column
+// block, row), split into runs of consecutive rows of one column block.
+struct ConvSeg {
+    int img, x0, y_s, len;
+};
+__device__ __forceinline__ ConvSeg conv_segment(long long u0, long long u_end, int H, int TPR) {
+    ConvSeg g;
+    g.y_s = int(u0 % H);
+    const long long t2 = u0 / H;
+    g.x0 = int(t2 % TPR) * 128;
+    g.img = int(t2 / TPR);
+    const long long end = (u0 - g.y_s + H) < u_end ? (u0 - g.y_s + H) : u_end;
+    g.len = int(end - u0);
+    return g;
+}
+
+// Persistent, warp-specialised conv kernel (320 threads = 10 warps). Work =
+// rows of 128-pixel column blocks, ordered (image, column block, row); each CTA
+// takes a contiguous range and walks down its column blocks with a ring of
+// halo rows in shared memory, so every input row is loaded once per block.
+//   warp 9 (loader)   cp.async of each halo row into the ring; arrival on
+//                     full[slot] when its copies land; waits on empty[slot]
+//   warp 8 (MMA)      one lane issues the 9 x CCH/2 MMAs of an output row into
+//                     one of two TMEM accumulators, then commits acc_full and
+//                     releases the rows it read last (empty[slot])
+//   warps 0-7 (epilogue) wait acc_full, tcgen05.ld, fused epilogue, stores;
+//                     arrive on acc_empty, and on empty[slot] of the centre
+//                     row (a residual equal to the input is read from the
+//                     ring), so a row is free after its last MMA and its
+//                     epilogue (edge rows of a run get their arrival at the
+//                     run's start and end)
+// Warp w of the epilogue reads TMEM lanes 32 (w % 4).. (its pixels) and the
+// column half w / 4; for NOUT = 16 only warps 0-3 work. Every wait is bounded;
+// a timeout sets the error flag and the role stops, and the others time out
+// in turn, so the kernel always ends.
 template <int CCH, int NOUT>
-__global__ void __launch_bounds__(256, 1) conv3x3_tc_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvArgs a) {
     using L = ConvLayout<CCH, NOUT>;
     constexpr int CIN = 8 * CCH;
     constexpr int NS = L::NS;
     constexpr int HP = L::HALO_PX;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t full_bar[NS], empty_bar[NS], accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ float bias_s[64];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -106,18 +144,24 @@ __global__ void __launch_bounds__(256, 1) conv3x3_tc_kernel(const ConvArgs a) {
     const long long u_end = T * (blockIdx.x + 1) / gridDim.x;
     uint8_t *As = smem + L::A_OFF;
     uint8_t *Bs = smem + L::B_OFF;
-    const __nv_bfloat16 *xg = static_cast<const __nv_bfloat16 *>(a.x);
 
     {
         const uint4 *src = static_cast<const uint4 *>(a.w);
-        for (int i = tid; i < 9 * CCH * NOUT; i += 256) cp_async16(Bs + i * 16, src + i);
+        for (int i = tid; i < 9 * CCH * NOUT; i += CONV_THREADS) cp_async16(Bs + i * 16, src + i);
         cp_async_commit();
         if (tid < 64) bias_s[tid] = (a.bias && tid < NOUT && a.epi != EPI_DGRAD) ? a.bias[tid] : 0.0f;
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_base_s, L::TMEM_COLS);
+    if (warp == CONV_MMA_WARP) tc::tmem_alloc(&tmem_base_s, L::TMEM_COLS);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&full_bar[s], 32);
+            tc::mbar_init(&empty_bar[s], 1 + CONV_EPI_WARPS);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&accf_bar[b], 1);
+            tc::mbar_init(&acce_bar[b], CONV_EPI_WARPS);
+        }
+        tc::mbar_init(&done_bar, 1);
         tc::fence_mbar_init();
     }
     cp_async_wait_0();
@@ -126,218 +170,220 @@ __global__ void __launch_bounds__(256, 1) conv3x3_tc_kernel(const ConvArgs a) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base_s;
-    constexpr uint32_t IDESC = tc::make_idesc_bf16(128, NOUT);
-    const uint32_t a_base = tc::smem_addr(As), b_base = tc::smem_addr(Bs);
-    constexpr uint32_t A_LBO = NS * HP * 16, A_SBO = 128;
-    constexpr uint32_t B_LBO = NOUT * 16, B_SBO = 128;
-    uint32_t ph[2] = {0u, 0u};
-    int issued[2] = {0, 0}, waited[2] = {0, 0};
-    bool failed = false;
 
-    // epilogue role
-    const int q = warp & 3, half = warp >> 2;
-    const bool epi_on = (NOUT >= 64) || half == 0;
-    const int m = 32 * q + lane;  // pixel within the column block (TMEM lane)
-    const int cb0 = (NOUT >= 64 ? 32 * half : 0);
-    const bool res_smem = a.epi == EPI_GELU && a.aux0 != nullptr && a.aux0 == a.x && CIN == NOUT;
-
-    for (long long u0 = u_begin; u0 < u_end && !failed;) {
-        // segment: consecutive rows of one column block of one image
-        const int y_s = int(u0 % H);
-        const long long t2 = u0 / H;
-        const int cbk = int(t2 % TPR);
-        const int img = int(t2 / TPR);
-        const long long seg_end = (u0 - y_s + H) < u_end ? (u0 - y_s + H) : u_end;
-        const int y_e = y_s + int(seg_end - u0) - 1;
-        const int x0 = cbk * 128;
-        const __nv_bfloat16 *ximg = xg + (size_t)img * H * W * CIN;
-        // rows are addressed relative to y_s - 1: slot(r) = (r - y_s + 1) % NS
-        auto load_row = [&](int r) {
-            int yy = r % H;
-            yy = yy < 0 ? yy + H : yy;
-            const int slot = (r - y_s + 1) % NS;
-            const __nv_bfloat16 *row = ximg + (size_t)yy * W * CIN;
-            for (int i = tid; i < CCH * HP; i += 256) {
-                const int px = i % HP, c = i / HP;
-                int xx = x0 + px - 1;
-                xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
-                cp_async16(As + ((c * NS + slot) * HP + px) * 16, row + (size_t)xx * CIN + 8 * c);
+    if (warp == CONV_LOAD_WARP) {
+        // ---------------- loader ----------------
+        const __nv_bfloat16 *xg = static_cast<const __nv_bfloat16 *>(a.x);
+        long long g = 0;  // running row counter (ring position)
+        bool ok = true;
+        for (long long u0 = u_begin; u0 < u_end && ok;) {
+            const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
+            const __nv_bfloat16 *ximg = xg + (size_t)sg.img * H * W * CIN;
+            for (int j = 0; j < sg.len + 2 && ok; ++j, ++g) {
+                const int slot = int(g % NS);
+                if (g >= NS && !tc::mbar_wait(&empty_bar[slot], uint32_t((g / NS - 1) & 1), CONV_WAIT_TRIES)) {
+                    ok = false;
+                    break;
+                }
+                int yy = (sg.y_s - 1 + j) % H;
+                yy = yy < 0 ? yy + H : yy;
+                const __nv_bfloat16 *row = ximg + (size_t)yy * W * CIN;
+                for (int i = lane; i < CCH * HP; i += 32) {
+                    const int c = i % CCH, px = i / CCH;
+                    int xx = sg.x0 + px - 1;
+                    xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+                    cp_async16(As + ((c * NS + slot) * HP + px) * 16, row + (size_t)xx * CIN + 8 * c);
+                }
+                cp_async_arrive_noinc(&full_bar[slot]);
             }
-        };
-        auto issue_mma = [&](int y, int acc) {
-            const uint32_t d = tmem + acc * L::ACC_COLS;
-            uint32_t accum = 0;
+            u0 += sg.len;
+        }
+        cp_async_wait_0();
+        if (!ok && lane == 0) atomicExch(a.error, 1);
+    } else if (warp == CONV_MMA_WARP) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t IDESC = tc::make_idesc_bf16(128, NOUT);
+        constexpr uint32_t A_LBO = NS * HP * 16, A_SBO = 128;
+        constexpr uint32_t B_LBO = NOUT * 16, B_SBO = 128;
+        const uint64_t ad0 = tc::make_desc(tc::smem_addr(As), A_LBO, A_SBO);
+        const uint64_t bd0 = tc::make_desc(tc::smem_addr(Bs), B_LBO, B_SBO);
+        const uint32_t a_lo0 = uint32_t(ad0), a_hi = uint32_t(ad0 >> 32);
+        const uint32_t b_lo0 = uint32_t(bd0), b_hi = uint32_t(bd0 >> 32);
+        long long g = 0, o = 0;
+        bool ok = true;
+        for (long long u0 = u_begin; u0 < u_end && ok;) {
+            const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
+            for (int i = 0; i < sg.len && ok; ++i, ++o) {
+                // rows g+i .. g+i+2 loaded (the first two were waited for by earlier rows)
+                for (int j = (i == 0 ? 0 : 2); j < 3; ++j) {
+                    const long long r = g + i + j;
+                    if (!tc::mbar_wait(&full_bar[r % NS], uint32_t((r / NS) & 1), CONV_WAIT_TRIES)) ok = false;
+                }
+                const int b = int(o & 1);
+                if (o >= 2 && !tc::mbar_wait(&acce_bar[b], uint32_t(((o >> 1) + 1) & 1), CONV_WAIT_TRIES)) ok = false;
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (lane == 0) {
+                    const uint32_t d = tmem + b * L::ACC_COLS;
+                    uint32_t accum = 0;
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                const int slot = (y - 1 + ky - y_s + 1) % NS;
+                    for (int ky = 0; ky < 3; ++ky) {
+                        const int slot = int((g + i + ky) % NS);
+                        const uint32_t a_row = a_lo0 + uint32_t(slot * HP);  // (slot * HP * 16) >> 4
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int t = ky * 3 + kx;
+                        for (int kx = 0; kx < 3; ++kx) {
+                            const int t = ky * 3 + kx;
 #pragma unroll
-                    for (int k2 = 0; k2 < CCH / 2; ++k2) {
-                        const uint64_t ad =
-                            tc::make_desc(a_base + (((2 * k2) * NS + slot) * HP + kx) * 16, A_LBO, A_SBO);
-                        const uint64_t bd = tc::make_desc(b_base + ((t * CCH + 2 * k2) * NOUT) * 16, B_LBO, B_SBO);
-                        tc::mma_bf16(d, ad, bd, IDESC, accum);
-                        accum = 1;
+                            for (int k2 = 0; k2 < CCH / 2; ++k2) {
+                                tc::mma_bf16_lohi(d, a_row + uint32_t((2 * k2) * NS * HP + kx), a_hi,
+                                                  b_lo0 + uint32_t((t * CCH + 2 * k2) * NOUT), b_hi, IDESC, accum);
+                                accum = 1;
+                            }
+                        }
+                    }
+                    tc::mma_commit(&accf_bar[b]);
+                    tc::mma_commit(&empty_bar[(g + i) % NS]);  // row g+i is not read again
+                    if (i == sg.len - 1) {
+                        tc::mma_commit(&empty_bar[(g + i + 1) % NS]);
+                        tc::mma_commit(&empty_bar[(g + i + 2) % NS]);
                     }
                 }
+                __syncwarp();
             }
-            tc::mma_commit(&mbar[acc]);
-        };
-        // prologue: rows y_s-1 .. y_s+1, then y_s+2
-        load_row(y_s - 1);
-        load_row(y_s);
-        load_row(y_s + 1);
-        cp_async_commit();
-        if (y_s + 1 <= y_e) load_row(y_s + 2);
-        cp_async_commit();
-        cp_async_wait_1();
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) issue_mma(y_s, y_s & 1);
-        issued[y_s & 1]++;
-        for (int y = y_s; y <= y_e; ++y) {
-            if (y + 2 <= y_e) load_row(y + 3);
-            cp_async_commit();
-            cp_async_wait_1();
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            if (__syncthreads_or(failed ? 1 : 0)) {
-                failed = true;
-                break;
-            }
-            tc::fence_after_sync();
-            if (y + 1 <= y_e) {
-                if (tid == 0) issue_mma(y + 1, (y + 1) & 1);
-                issued[(y + 1) & 1]++;
-            }
-            const int acc = y & 1;
+            g += sg.len + 2;
+            u0 += sg.len;
+        }
+        if (lane == 0) {
+            tc::mma_commit(&done_bar);  // tracks every MMA issued above
+            if (!tc::mbar_wait(&done_bar, 0u, CONV_WAIT_TRIES)) ok = false;
+        }
+        __syncwarp();
+        if (!ok && lane == 0) atomicExch(a.error, 1);
+    } else {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3, half = warp >> 2;
+        const bool epi_on = (NOUT >= 64) || half == 0;
+        const int m = 32 * q + lane;
+        const int cb0 = (NOUT >= 64 ? 32 * half : 0);
+        constexpr int NC = NOUT < 32 ? NOUT : 32;
+        const bool res_smem = a.epi == EPI_GELU && a.aux0 != nullptr && a.aux0 == a.x && CIN == NOUT;
+        long long o = 0, g = 0;
+        bool ok = true;
+        for (long long u0 = u_begin; u0 < u_end && ok;) {
+            const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
             __syncwarp();
-            if (!tc::mbar_wait(&mbar[acc], ph[acc], 1u << 22)) {
-                failed = true;
-                if (lane == 0) atomicExch(a.error, 1);
-            }
-            ph[acc] ^= 1u;
-            waited[acc]++;
-            tc::fence_after_sync();
-            if (!epi_on || failed) continue;
-            // ---- fused epilogue of row y: pixel p, channels cb0 .. cb0+31 ----
-            const size_t p = ((size_t)img * H + y) * W + x0 + m;
-            float v[32];
-            tc::tmem_ld32(tmem + acc * L::ACC_COLS + cb0 + (uint32_t(32 * q) << 16), v);
-            constexpr int NC = NOUT < 32 ? NOUT : 32;
+            if (lane == 0) mbar_arrive(&empty_bar[g % NS]);  // first halo row: no epilogue reads it
+            for (int i = 0; i < sg.len; ++i, ++o) {
+                const int b = int(o & 1);
+                if (!tc::mbar_wait(&accf_bar[b], uint32_t((o >> 1) & 1), CONV_WAIT_TRIES)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                if (epi_on) {
+                    const int y = sg.y_s + i;
+                    const size_t p = ((size_t)sg.img * H + y) * W + sg.x0 + m;
+                    float v[32];
+                    tc::tmem_ld32(tmem + b * L::ACC_COLS + cb0 + (uint32_t(32 * q) << 16), v);
 #pragma unroll
-            for (int i = 0; i < NC; ++i) v[i] += bias_s[cb0 + i];
-            if (a.epi == EPI_GELU) {
-                float r[32];
-                if (res_smem) {
-                    const int slot = (y - y_s + 1) % NS;
+                    for (int k = 0; k < NC; ++k) v[k] += bias_s[cb0 + k];
+                    if (a.epi == EPI_GELU) {
+                        const uint4 *rp =
+                            res_smem ? reinterpret_cast<const uint4 *>(
+                                           As + (((cb0 / 8) * NS + int((g + i + 1) % NS)) * HP + m + 1) * 16)
+                            : a.aux0 ? reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(a.aux0) +
+                                                                       p * NOUT + cb0)
+                                     : nullptr;
+                        const int rstride = res_smem ? NS * HP : 1;  // uint4 steps between 8-channel chunks
+                        uint4 *ao = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out1) + p * NOUT + cb0);
+                        uint4 *zo = a.out0 ? reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out0) +
+                                                                       p * NOUT + cb0)
+                                           : nullptr;
 #pragma unroll
-                    for (int c4 = 0; c4 < 4; ++c4) {
-                        const uint4 w4 = *reinterpret_cast<const uint4 *>(
-                            As + (((cb0 / 8 + c4) * NS + slot) * HP + m + 1) * 16);
-                        const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+                        for (int c4 = 0; c4 < NC / 8; ++c4) {
+                            float g8[8];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            r[8 * c4 + 2 * k] = __uint_as_float(ww[k] << 16);
-                            r[8 * c4 + 2 * k + 1] = __uint_as_float(ww[k] & 0xffff0000u);
+                            for (int k = 0; k < 8; ++k) g8[k] = gelu_f(v[8 * c4 + k]);
+                            if (rp) {
+                                const uint4 w4 = rp[c4 * rstride];
+                                const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    g8[2 * k] += __uint_as_float(ww[k] << 16);
+                                    g8[2 * k + 1] += __uint_as_float(ww[k] & 0xffff0000u);
+                                }
+                            }
+                            ao[c4] = make_uint4(bf2(g8[0], g8[1]), bf2(g8[2], g8[3]), bf2(g8[4], g8[5]),
+                                                bf2(g8[6], g8[7]));
+                            if (zo) {
+                                const float *z = v + 8 * c4;
+                                zo[c4] = make_uint4(bf2(z[0], z[1]), bf2(z[2], z[3]), bf2(z[4], z[5]),
+                                                    bf2(z[6], z[7]));
+                            }
                         }
-                    }
-                } else if (a.aux0) {
-                    const uint4 *rp = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(a.aux0) +
-                                                                      p * NOUT + cb0);
+                    } else if (a.epi == EPI_LINEAR) {
+                        float4 *op = reinterpret_cast<float4 *>(static_cast<float *>(a.out0) + p * NOUT + cb0);
 #pragma unroll
-                    for (int c4 = 0; c4 < NC / 8; ++c4) {
-                        const uint4 w4 = rp[c4];
-                        const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+                        for (int k = 0; k < NC / 4; ++k)
+                            op[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    } else if (a.epi == EPI_DGRAD) {
+                        const float4 *gin = a.aux0 ? reinterpret_cast<const float4 *>(
+                                                         static_cast<const float *>(a.aux0) + p * NOUT + cb0)
+                                                   : nullptr;
+                        float4 *go = reinterpret_cast<float4 *>(static_cast<float *>(a.out0) + p * NOUT + cb0);
+                        const uint4 *zp = reinterpret_cast<const uint4 *>(
+                            static_cast<const __nv_bfloat16 *>(a.zprev) + p * NOUT + cb0);
+                        uint4 *dz = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out1) + p * NOUT + cb0);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            r[8 * c4 + 2 * k] = __uint_as_float(ww[k] << 16);
-                            r[8 * c4 + 2 * k + 1] = __uint_as_float(ww[k] & 0xffff0000u);
+                        for (int c4 = 0; c4 < NC / 8; ++c4) {
+                            float g8[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) g8[k] = v[8 * c4 + k];
+                            if (gin) {
+                                const float4 g0 = gin[2 * c4], g1 = gin[2 * c4 + 1];
+                                g8[0] += g0.x; g8[1] += g0.y; g8[2] += g0.z; g8[3] += g0.w;
+                                g8[4] += g1.x; g8[5] += g1.y; g8[6] += g1.z; g8[7] += g1.w;
+                            }
+                            go[2 * c4] = make_float4(g8[0], g8[1], g8[2], g8[3]);
+                            go[2 * c4 + 1] = make_float4(g8[4], g8[5], g8[6], g8[7]);
+                            const uint4 z4 = zp[c4];
+                            const uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
+                            float d[8];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                d[2 * k] = g8[2 * k] * gelu_grad(__uint_as_float(zz[k] << 16));
+                                d[2 * k + 1] = g8[2 * k + 1] * gelu_grad(__uint_as_float(zz[k] & 0xffff0000u));
+                            }
+                            dz[c4] = make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
                         }
-                    }
-                } else {
+                    } else if (cb0 == 0) {  // EPI_QUPDATE: channels 0..5
+                        const size_t P = (size_t)H * W;
+                        const size_t pix = (size_t)y * W + sg.x0 + m;
+                        const float *qi = static_cast<const float *>(a.aux0) + (size_t)sg.img * 6 * P;
+                        float *qo = static_cast<float *>(a.out0) + (size_t)sg.img * 6 * P;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) r[i] = 0.0f;
-                }
-                uint4 *ao = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out1) + p * NOUT + cb0);
-#pragma unroll
-                for (int c4 = 0; c4 < NC / 8; ++c4) {
-                    float g[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) g[k] = gelu_f(v[8 * c4 + k]) + r[8 * c4 + k];
-                    ao[c4] = make_uint4(bf2(g[0], g[1]), bf2(g[2], g[3]), bf2(g[4], g[5]), bf2(g[6], g[7]));
-                }
-                if (a.out0) {
-                    uint4 *zo = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out0) + p * NOUT + cb0);
-#pragma unroll
-                    for (int c4 = 0; c4 < NC / 8; ++c4) {
-                        const float *z = v + 8 * c4;
-                        zo[c4] = make_uint4(bf2(z[0], z[1]), bf2(z[2], z[3]), bf2(z[4], z[5]), bf2(z[6], z[7]));
+                        for (int c = 0; c < 6; ++c) qo[c * P + pix] = qi[c * P + pix] + a.scale * v[c];
                     }
                 }
-            } else if (a.epi == EPI_LINEAR) {
-                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out0) + p * NOUT + cb0);
-#pragma unroll
-                for (int i = 0; i < NC / 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            } else if (a.epi == EPI_DGRAD) {
-                const float4 *gin =
-                    a.aux0 ? reinterpret_cast<const float4 *>(static_cast<const float *>(a.aux0) + p * NOUT + cb0)
-                           : nullptr;
-                float4 *go = reinterpret_cast<float4 *>(static_cast<float *>(a.out0) + p * NOUT + cb0);
-                const uint4 *zp =
-                    reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(a.zprev) + p * NOUT + cb0);
-                uint4 *dz = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out1) + p * NOUT + cb0);
-#pragma unroll
-                for (int c4 = 0; c4 < NC / 8; ++c4) {
-                    float g[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) g[k] = v[8 * c4 + k];
-                    if (gin) {
-                        const float4 g0 = gin[2 * c4], g1 = gin[2 * c4 + 1];
-                        g[0] += g0.x; g[1] += g0.y; g[2] += g0.z; g[3] += g0.w;
-                        g[4] += g1.x; g[5] += g1.y; g[6] += g1.z; g[7] += g1.w;
-                    }
-                    go[2 * c4] = make_float4(g[0], g[1], g[2], g[3]);
-                    go[2 * c4 + 1] = make_float4(g[4], g[5], g[6], g[7]);
-                    const uint4 z4 = zp[c4];
-                    const uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
-                    float d[8];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        d[2 * k] = g[2 * k] * gelu_grad(__uint_as_float(zz[k] << 16));
-                        d[2 * k + 1] = g[2 * k + 1] * gelu_grad(__uint_as_float(zz[k] & 0xffff0000u));
-                    }
-                    dz[c4] = make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&acce_bar[b]);
+                    mbar_arrive(&empty_bar[(g + i + 1) % NS]);  // centre row of output row i
                 }
-            } else if (cb0 == 0) {  // EPI_QUPDATE: channels 0..5
-                const size_t P = (size_t)H * W;
-                const size_t pix = (size_t)y * W + x0 + m;
-                const float *qi = static_cast<const float *>(a.aux0) + (size_t)img * 6 * P;
-                float *qo = static_cast<float *>(a.out0) + (size_t)img * 6 * P;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) qo[c * P + pix] = qi[c * P + pix] + a.scale * v[c];
             }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[(g + sg.len + 1) % NS]);  // last halo row
+            g += sg.len + 2;
+            u0 += sg.len;
         }
-        if (__syncthreads_or(failed ? 1 : 0)) failed = true;  // uniform exit after a segment
-        u0 = seg_end;
-    }
-    // drain: let outstanding copies and MMAs finish (bounded) before TMEM is freed
-    cp_async_wait_0();
-    for (int b = 0; b < 2; ++b) {
-        while (waited[b] < issued[b]) {
-            if (!tc::mbar_wait(&mbar[b], ph[b], 1u << 22) && lane == 0) atomicExch(a.error, 1);
-            ph[b] ^= 1u;
-            waited[b]++;
-        }
+        if (!ok && lane == 0) atomicExch(a.error, 1);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
+    if (warp == CONV_MMA_WARP) tc::tmem_dealloc(tmem, L::TMEM_COLS);
 }
 
 template <int CCH, int NOUT>
@@ -351,8 +397,236 @@ cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long rows = (long long)a.nimg * a.H * (a.W / 128);
     const int grid = rows < sms ? int(rows) : sms;
-    conv3x3_tc_kernel<CCH, NOUT><<<grid, 256, L::SMEM, st>>>(a);
+    conv3x3_tc_kernel<CCH, NOUT><<<grid, CONV_THREADS, L::SMEM, st>>>(a);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores:
+//   dW[n][c][ky][kx] = sum_p g[p][n] x[p + (ky-1, kx-1)][c]
+// as D[m][n] = sum_k A[m][k] B[n][k] with K = pixels and both operands
+// MN-major (NHWC rows give 8 consecutive channels per 16 bytes). A rows are
+// (ky, c) for two consecutive halo rows stacked in M = 128 (ky = 0, 1 in one
+// tile; ky = 2 and an unused half in the other); kx is a 16-byte shift of the
+// start address along K. Six accumulator tiles (2 row pairs x 3 kx) of N = NT
+// columns stay in TMEM for all of a CTA's rows; at the end each CTA writes its
+// partial sums [9][NT][64] (FP32), reduced over CTAs in a fixed order later.
+// The x ring has one mirror slot after the last, a copy of slot 0, so that two
+// consecutive rows are always adjacent in memory. Source x may have 16 or 64
+// channels (16: the other chunks stay zero).
+// ---------------------------------------------------------------------------
+template <int NT>
+struct WgradLayout {
+    static constexpr int HP = 130;
+    static constexpr int NSX = 6;
+    static constexpr int XSLOT = 8 * HP * 16;
+    static constexpr int X_BYTES = (NSX + 1) * XSLOT;
+    static constexpr int NSG = 4;
+    static constexpr int GSLOT = (NT / 8) * 128 * 16;
+    static constexpr int G_OFF = ((X_BYTES + 1023) / 1024) * 1024;
+    static constexpr int SMEM = G_OFF + NSG * GSLOT;
+    static constexpr int TMEM_COLS = NT == 64 ? 512 : 128;  // 6 tiles x NT columns
+};
+
+template <int CS, int NT>
+__global__ void __launch_bounds__(CONV_THREADS, 1) wgrad_tc_kernel(const WgradArgs a) {
+    using L = WgradLayout<NT>;
+    constexpr int NSX = L::NSX, NSG = L::NSG, HP = L::HP;
+    constexpr int CCS = CS / 8;  // source chunks per pixel
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t xf_bar[NSX], xe_bar[NSX], gf_bar[NSG], ge_bar[NSG], done_bar;
+    __shared__ uint32_t tmem_base_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int H = a.H, W = a.W;
+    const int TPR = W / 128;
+    const long long T = (long long)a.nimg * TPR * H;
+    const long long u_begin = T * blockIdx.x / gridDim.x;
+    const long long u_end = T * (blockIdx.x + 1) / gridDim.x;
+    uint8_t *Xs = smem;
+    uint8_t *Gs = smem + L::G_OFF;
+
+    for (int i = tid; i < L::X_BYTES / 16; i += CONV_THREADS) reinterpret_cast<uint4 *>(Xs)[i] = make_uint4(0, 0, 0, 0);
+    if (warp == CONV_MMA_WARP) tc::tmem_alloc(&tmem_base_s, L::TMEM_COLS);
+    if (tid == 0) {
+        for (int s = 0; s < NSX; ++s) {
+            tc::mbar_init(&xf_bar[s], 32);
+            tc::mbar_init(&xe_bar[s], 1);
+        }
+        for (int s = 0; s < NSG; ++s) {
+            tc::mbar_init(&gf_bar[s], 32);
+            tc::mbar_init(&ge_bar[s], 1);
+        }
+        tc::mbar_init(&done_bar, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == CONV_LOAD_WARP) {
+        const __nv_bfloat16 *xg = static_cast<const __nv_bfloat16 *>(a.x);
+        const __nv_bfloat16 *gg = static_cast<const __nv_bfloat16 *>(a.g);
+        long long gx = 0, gn = 0;
+        bool ok = true;
+        auto load_x = [&](const ConvSeg &sg, int j) -> bool {
+            const int slot = int(gx % NSX);
+            if (gx >= NSX && !tc::mbar_wait(&xe_bar[slot], uint32_t((gx / NSX - 1) & 1), CONV_WAIT_TRIES)) return false;
+            int yy = (sg.y_s - 1 + j) % H;
+            yy = yy < 0 ? yy + H : yy;
+            const __nv_bfloat16 *row = xg + ((size_t)sg.img * H + yy) * W * CS;
+            for (int i = lane; i < CCS * HP; i += 32) {
+                const int c = i % CCS, px = i / CCS;
+                int xx = sg.x0 + px - 1;
+                xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+                const __nv_bfloat16 *src = row + (size_t)xx * CS + 8 * c;
+                cp_async16(Xs + ((slot * 8 + c) * HP + px) * 16, src);
+                if (slot == 0) cp_async16(Xs + ((NSX * 8 + c) * HP + px) * 16, src);
+            }
+            cp_async_arrive_noinc(&xf_bar[slot]);
+            ++gx;
+            return true;
+        };
+        auto load_g = [&](const ConvSeg &sg, int i) -> bool {
+            const int slot = int(gn % NSG);
+            if (gn >= NSG && !tc::mbar_wait(&ge_bar[slot], uint32_t((gn / NSG - 1) & 1), CONV_WAIT_TRIES)) return false;
+            const __nv_bfloat16 *row = gg + (((size_t)sg.img * H + sg.y_s + i) * W + sg.x0) * NT;
+            for (int k = lane; k < (NT / 8) * 128; k += 32) {
+                const int c = k % (NT / 8), px = k / (NT / 8);
+                cp_async16(Gs + slot * L::GSLOT + (c * 128 + px) * 16, row + (size_t)px * NT + 8 * c);
+            }
+            cp_async_arrive_noinc(&gf_bar[slot]);
+            ++gn;
+            return true;
+        };
+        for (long long u0 = u_begin; u0 < u_end && ok;) {
+            const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
+            ok = load_x(sg, 0) && load_x(sg, 1);
+            for (int i = 0; i < sg.len && ok; ++i) ok = load_x(sg, i + 2) && load_g(sg, i);
+            u0 += sg.len;
+        }
+        cp_async_wait_0();
+        if (!ok && lane == 0) atomicExch(a.error, 1);
+    } else if (warp == CONV_MMA_WARP) {
+        constexpr uint32_t IDESC = tc::make_idesc_bf16(128, NT) | (1u << 15) | (1u << 16);  // A, B MN-major
+        const uint32_t x_base = tc::smem_addr(Xs), g_base = tc::smem_addr(Gs);
+        // MN-major, no swizzle: a core matrix is 8 k-rows x 16 B (8 channels);
+        // the leading byte offset steps along K (128 B: the next 8 pixels), the
+        // stride byte offset along M/N (the next 8-channel chunk).
+        constexpr uint32_t A_LBO = 128, A_SBO = HP * 16;
+        constexpr uint32_t B_LBO = 128, B_SBO = 128 * 16;
+        const uint64_t ad0 = tc::make_desc(x_base, A_LBO, A_SBO), bd0 = tc::make_desc(g_base, B_LBO, B_SBO);
+        const uint32_t a_lo0 = uint32_t(ad0), a_hi = uint32_t(ad0 >> 32);
+        const uint32_t b_lo0 = uint32_t(bd0), b_hi = uint32_t(bd0 >> 32);
+        long long gx = 0, gn = 0;
+        bool ok = true, first = true;
+        for (long long u0 = u_begin; u0 < u_end && ok;) {
+            const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
+            for (int i = 0; i < sg.len && ok; ++i, ++gn) {
+                for (int j = (i == 0 ? 0 : 2); j < 3; ++j) {
+                    const long long r = gx + i + j;
+                    if (!tc::mbar_wait(&xf_bar[r % NSX], uint32_t((r / NSX) & 1), CONV_WAIT_TRIES)) ok = false;
+                }
+                if (!tc::mbar_wait(&gf_bar[gn % NSG], uint32_t((gn / NSG) & 1), CONV_WAIT_TRIES)) ok = false;
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (lane == 0) {
+                    const uint32_t s0 = uint32_t((gx + i) % NSX), s2 = uint32_t((gx + i + 2) % NSX);
+                    const uint32_t g_lo = b_lo0 + uint32_t(gn % NSG) * (L::GSLOT >> 4);
+                    const uint32_t a0_lo = a_lo0 + s0 * 8 * HP, a1_lo = a_lo0 + s2 * 8 * HP;
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) {
+                            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                            tc::mma_bf16_lohi(tmem + kx * NT, a0_lo + kx + 16 * kk, a_hi, g_lo + 16 * kk, b_hi, IDESC,
+                                              acc);
+                            tc::mma_bf16_lohi(tmem + (3 + kx) * NT, a1_lo + kx + 16 * kk, a_hi, g_lo + 16 * kk, b_hi,
+                                              IDESC, acc);
+                        }
+                    }
+                    tc::mma_commit(&ge_bar[gn % NSG]);
+                    tc::mma_commit(&xe_bar[(gx + i) % NSX]);
+                    if (i == sg.len - 1) {
+                        tc::mma_commit(&xe_bar[(gx + i + 1) % NSX]);
+                        tc::mma_commit(&xe_bar[(gx + i + 2) % NSX]);
+                    }
+                }
+                first = false;
+                __syncwarp();
+            }
+            gx += sg.len + 2;
+            u0 += sg.len;
+        }
+        if (lane == 0) tc::mma_commit(&done_bar);
+        __syncwarp();
+        if (!ok && lane == 0) atomicExch(a.error, 1);
+    }
+    if (warp < CONV_EPI_WARPS) {
+        // epilogue: partial sums of this CTA
+        const bool ok = tc::mbar_wait(&done_bar, 0u, CONV_WAIT_TRIES);
+        if (!ok && lane == 0) atomicExch(a.error, 1);
+        tc::fence_after_sync();
+        const int q = warp & 3, half = warp >> 2;
+        const int m = 32 * q + lane;
+        const int c = m & 63;
+        float *part = a.part + (size_t)blockIdx.x * 9 * NT * 64;
+        if (ok && (NT == 64 || half == 0)) {
+            for (int pr = 0; pr < 2; ++pr) {
+                const int ky = 2 * pr + (m >> 6);
+                for (int kx = 0; kx < 3; ++kx) {
+                    float v[32];
+                    if (NT == 64) {
+                        tc::tmem_ld32(tmem + (pr * 3 + kx) * NT + 32 * half + (uint32_t(32 * q) << 16), v);
+                        if (ky <= 2) {
+                            float *o = part + ((size_t)(ky * 3 + kx) * NT + 32 * half) * 64 + c;
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) o[k * 64] = v[k];
+                        }
+                    } else {
+                        tc::tmem_ld32(tmem + (pr * 3 + kx) * NT + (uint32_t(32 * q) << 16), v);  // 16 used
+                        if (ky <= 2) {
+                            float *o = part + ((size_t)(ky * 3 + kx) * NT) * 64 + c;
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) o[k * 64] = v[k];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == CONV_MMA_WARP) tc::tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
+template <int CS, int NT>
+cudaError_t launch_wgrad_t(const WgradArgs &a, int grid, cudaStream_t st) {
+    using L = WgradLayout<NT>;
+    cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<CS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L::SMEM);
+    if (e != cudaSuccess) return e;
+    wgrad_tc_kernel<CS, NT><<<grid, CONV_THREADS, L::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+int wgrad_grid(const WgradArgs &a) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long rows = (long long)a.nimg * a.H * (a.W / 128);
+    return rows < sms ? int(rows) : sms;
+}
+
+cudaError_t launch_wgrad_tc(const WgradArgs &a, int *grid_out, cudaStream_t st) {
+    const int grid = wgrad_grid(a);
+    if (grid_out) *grid_out = grid;
+    if (a.cs == 64 && a.nt == 64) return launch_wgrad_t<64, 64>(a, grid, st);
+    if (a.cs == 16 && a.nt == 64) return launch_wgrad_t<16, 64>(a, grid, st);
+    if (a.cs == 64 && a.nt == 16) return launch_wgrad_t<64, 16>(a, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 bool conv_supported(int cin, int nout) {

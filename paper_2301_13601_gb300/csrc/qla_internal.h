@@ -106,6 +106,21 @@ struct ConvArgs {
 bool conv_supported(int cin, int nout);
 cudaError_t launch_conv(int cin, int nout, const ConvArgs &a, cudaStream_t st);
 
+// Weight gradient of a 3x3 circular conv on the tensor cores: per-CTA partial
+// sums part[cta][9][nt][64] of sum_p g[p][n] x[p + tap][c]; x BF16 [..][cs]
+// (cs = 16 or 64), g BF16 [..][nt] (nt = 64 or 16). *grid_out = CTAs used.
+struct WgradArgs {
+    const void *x;
+    int cs;
+    const void *g;
+    int nt;
+    int nimg, H, W;
+    float *part;
+    int *error;
+};
+int wgrad_grid(const WgradArgs &a);
+cudaError_t launch_wgrad_tc(const WgradArgs &a, int *grid_out, cudaStream_t st);
+
 // Weight packing modes: plain, adjoint (transpose + 180-degree flip), and
 // plain with the input channels of the surrogate's first layer
 // (packed c: 0-5 -> logical c, 6-11 -> logical c-6, 12-14 -> logical c-6, 15 -> 0).

@@ -4,8 +4,8 @@
 //   a0 = GELU(conv0(x0));  a_l = a_{l-1} + GELU(conv_l(a_{l-1})), l = 1..4;
 //   f  = conv5(a4)   (3x3 circular convolutions, 64 hidden channels).
 // The forward and input-gradient convolutions run on the tcgen05 tensor cores
-// (qla_conv.cu); the weight gradients are an FP32 CUDA-core reduction over
-// pixels; the optimiser is Adam on FP32 master weights that are re-packed to
+// (qla_conv.cu), and so do the weight gradients (pixels as the reduction
+// dimension, per-CTA partial sums reduced in a fixed order); the optimiser is Adam on FP32 master weights that are re-packed to
 // BF16 after every update. The input x0 carries each field as two BF16 parts
 // (high and low) that share first-layer weights, so the network sees the
 // FP32 state to about 16 significant bits, plus n in BF16.
@@ -35,7 +35,7 @@ constexpr int CINP[NL] = {16, 64, 64, 64, 64, 64};  // packed input channels
 constexpr int NOUT[NL] = {64, 64, 64, 64, 64, 6};   // logical output channels
 constexpr int NOUTP[NL] = {64, 64, 64, 64, 64, 16};
 constexpr int X0C = 16;                              // x0 channels: Q hi (6), Q lo (6), n (3), 0
-constexpr int WSPLIT = 64;                           // pixel splits of the weight-gradient reduction
+constexpr int BIAS_BLOCKS = 256;                     // pixel splits of the bias-gradient reduction
 constexpr int RED_BLOCKS = 512;                      // partial sums of the loss reductions
 
 __device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
@@ -136,85 +136,38 @@ __global__ void loss_grad_kernel(const float *__restrict__ f, const float *__res
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// ---- weight gradient: dW[n][c][t] = sum_p g[p][n] x[p + off_t][c] ---------
-// CT = channels of x, NT = channels of g; CTA = (pixel split, tap); each
-// thread owns a 4 x 4 block of (n, c). Pixels go through shared memory in
-// chunks of 32 (a chunk never crosses a row: W is a multiple of 128).
-template <int CT, int NT>
-__global__ void __launch_bounds__(CT *NT / 16) wgrad_kernel(const __nv_bfloat16 *__restrict__ x,
-                                                            const __nv_bfloat16 *__restrict__ g, int H, int W,
-                                                            long long NP, long long px_per_split,
-                                                            float *__restrict__ part, float *__restrict__ bpart) {
-    constexpr int NTH = CT * NT / 16;
-    constexpr int KP = 32;
-    __shared__ __align__(16) float Gs[KP][NT];
-    __shared__ __align__(16) float Xs[KP][CT];
-    const int tap = blockIdx.y, ky = tap / 3, kx = tap % 3;
-    const int s = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int tn = tid / (CT / 4), tc = tid % (CT / 4);
-    const long long P = (long long)H * W;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-    float bacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const bool do_bias = (tap == 4) && (tc == 0);
-    const long long p_begin = s * px_per_split;
-    const long long p_end = p_begin + px_per_split < NP ? p_begin + px_per_split : NP;
-    for (long long p0 = p_begin; p0 < p_end; p0 += KP) {
-        const long long img = p0 / P;
-        const long long rem = p0 - img * P;
-        const int y = int(rem / W), x0c = int(rem - (long long)y * W);
-        int ys = y + ky - 1;
-        ys = ys < 0 ? ys + H : (ys >= H ? ys - H : ys);
-        const long long qrow = img * P + (long long)ys * W;
-        for (int i = tid; i < KP * NT / 8; i += NTH) {
-            const int px = i / (NT / 8), ch = (i % (NT / 8)) * 8;
-            const uint4 v = *reinterpret_cast<const uint4 *>(g + (p0 + px) * NT + ch);
-            *reinterpret_cast<float4 *>(&Gs[px][ch]) = make_float4(bf_lo(v.x), bf_hi(v.x), bf_lo(v.y), bf_hi(v.y));
-            *reinterpret_cast<float4 *>(&Gs[px][ch + 4]) = make_float4(bf_lo(v.z), bf_hi(v.z), bf_lo(v.w), bf_hi(v.w));
-        }
-        for (int i = tid; i < KP * CT / 8; i += NTH) {
-            const int px = i / (CT / 8), ch = (i % (CT / 8)) * 8;
-            int xs = x0c + px + kx - 1;
-            xs = xs < 0 ? xs + W : (xs >= W ? xs - W : xs);
-            const uint4 v = *reinterpret_cast<const uint4 *>(x + (qrow + xs) * CT + ch);
-            *reinterpret_cast<float4 *>(&Xs[px][ch]) = make_float4(bf_lo(v.x), bf_hi(v.x), bf_lo(v.y), bf_hi(v.y));
-            *reinterpret_cast<float4 *>(&Xs[px][ch + 4]) = make_float4(bf_lo(v.z), bf_hi(v.z), bf_lo(v.w), bf_hi(v.w));
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int px = 0; px < KP; ++px) {
-            const float4 gv = *reinterpret_cast<const float4 *>(&Gs[px][4 * tn]);
-            const float4 xv = *reinterpret_cast<const float4 *>(&Xs[px][4 * tc]);
-            const float ga[4] = {gv.x, gv.y, gv.z, gv.w};
-            const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ga[i], xa[j], acc[i][j]);
-                if (do_bias) bacc[i] += ga[i];
-            }
-        }
-        __syncthreads();
+// ---- bias gradient: partial sums of g over pixel ranges -------------------
+// 16-byte loads: NT/8 threads per pixel, 256 / (NT/8) pixels per pass.
+template <int NT>
+__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ g, long long NP, float *__restrict__ bpart) {
+    constexpr int TPP = NT / 8;       // threads per pixel
+    constexpr int PPB = 256 / TPP;    // pixels per pass
+    __shared__ float sh[PPB][NT + 1];
+    const int c8 = threadIdx.x % TPP, pl = threadIdx.x / TPP;
+    const long long per = (NP + gridDim.x - 1) / gridDim.x;
+    const long long b = blockIdx.x * per, e = b + per < NP ? b + per : NP;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long p = b + pl; p < e; p += PPB) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(g + p * NT + 8 * c8);
+        acc[0] += bf_lo(v.x); acc[1] += bf_hi(v.x); acc[2] += bf_lo(v.y); acc[3] += bf_hi(v.y);
+        acc[4] += bf_lo(v.z); acc[5] += bf_hi(v.z); acc[6] += bf_lo(v.w); acc[7] += bf_hi(v.w);
     }
-    float *o = part + ((size_t(s) * 9 + tap) * NT) * CT;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4 *>(o + (4 * tn + i) * CT + 4 * tc) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    if (do_bias) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) bpart[size_t(s) * NT + 4 * tn + i] = bacc[i];
+    for (int k = 0; k < 8; ++k) sh[pl][8 * c8 + k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < NT) {
+        float t = 0.0f;
+        for (int k = 0; k < PPB; ++k) t += sh[k][threadIdx.x];
+        bpart[size_t(blockIdx.x) * NT + threadIdx.x] = t;
     }
 }
 
-// Sum the splits in a fixed order into the logical gradient layout
-// gw[n][c][ky][kx], gb[n]; tied: packed input channels c and c+6 (c < 6) both
-// belong to logical c, packed 12-14 to logical 6-8.
-__global__ void wgrad_reduce_kernel(const float *__restrict__ part, const float *__restrict__ bpart, int S, int NT,
-                                    int CT, int nout, int cin, int tied, float *__restrict__ gw,
+// Sum the per-CTA partials part[S][9][NT][CT] and bias partials bpart[SB][NT]
+// in a fixed order into the logical gradient layout gw[n][c][ky][kx], gb[n];
+// tied: packed input channels c and c+6 (c < 6) both belong to logical c,
+// packed 12-14 to logical 6-8.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int S, const float *__restrict__ bpart, int SB,
+                                    int NT, int CT, int nout, int cin, int tied, float *__restrict__ gw,
                                     float *__restrict__ gb) {
     const int total = nout * cin * 9;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,7 +185,7 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, const float 
     } else if (i < total + nout) {
         const int n = i - total;
         float acc = 0.0f;
-        for (int s = 0; s < S; ++s) acc += bpart[size_t(s) * NT + n];
+        for (int s = 0; s < SB; ++s) acc += bpart[size_t(s) * NT + n];
         gb[n] = acc;
     }
 }
@@ -396,18 +349,29 @@ qla_status forward_train(qla_surrogate *s, const float *q_in, const float *n, cu
                 nullptr, 1.0f, st);
 }
 
-template <int CT, int NT>
-qla_status wgrad(qla_surrogate *s, int l, const void *x, const void *g, cudaStream_t st) {
-    long long per = (s->NP + WSPLIT - 1) / WSPLIT;
-    per = (per + 31) / 32 * 32;
-    dim3 grid(WSPLIT, 9);
-    wgrad_kernel<CT, NT><<<grid, CT * NT / 16, 0, st>>>(static_cast<const __nv_bfloat16 *>(x),
-                                                        static_cast<const __nv_bfloat16 *>(g), s->cfg.H, s->cfg.W,
-                                                        s->NP, per, s->wpart, s->bpart);
+// Weight and bias gradient of layer l: x = the layer's input (cs channels),
+// g = dL/dz of the layer (nt channels).
+qla_status wgrad(qla_surrogate *s, int l, const void *x, int cs, const void *g, int nt, cudaStream_t st) {
+    WgradArgs w;
+    w.x = x;
+    w.cs = cs;
+    w.g = g;
+    w.nt = nt;
+    w.nimg = s->cfg.nimg;
+    w.H = s->cfg.H;
+    w.W = s->cfg.W;
+    w.part = s->wpart;
+    w.error = s->err;
+    int S = 0;
+    SG_CUDA(s, launch_wgrad_tc(w, &S, st));
+    if (nt == 64)
+        bias_grad_kernel<64><<<BIAS_BLOCKS, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(g), s->NP, s->bpart);
+    else
+        bias_grad_kernel<16><<<BIAS_BLOCKS, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(g), s->NP, s->bpart);
     SG_CUDA(s, cudaGetLastError());
     const int total = NOUT[l] * CIN[l] * 9 + NOUT[l];
-    wgrad_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->wpart, s->bpart, WSPLIT, NT, CT, NOUT[l], CIN[l],
-                                                             l == 0 ? 1 : 0, s->grads + s->off_w[l],
+    wgrad_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->wpart, S, s->bpart, BIAS_BLOCKS, nt, 64, NOUT[l],
+                                                             CIN[l], l == 0 ? 1 : 0, s->grads + s->off_w[l],
                                                              s->grads + s->off_b[l]);
     SG_CUDA(s, cudaGetLastError());
     return QLA_OK;
@@ -431,16 +395,16 @@ qla_status loss_and_grad(qla_surrogate *s, const float *q_in, const float *n, co
     // layer 5: dgrad into da_4 (a_4 feeds only layer 5), dz_4 = da_4 GELU'(z_4)
     r = conv(s, NOUTP[5], HID, s->g6, s->wb[5], nullptr, QLA_EPI_DGRAD, nullptr, s->z[4], s->da[0], s->dz[0], 1.0f,
              st);
-    if (r == QLA_OK) r = wgrad<HID, 16>(s, 5, s->act[4], s->g6, st);
+    if (r == QLA_OK) r = wgrad(s, 5, s->act[4], HID, s->g6, 16, st);
     // layers 4..1: da_{l-1} = da_l + dgrad_l(dz_l); dz_{l-1} = da_{l-1} GELU'(z_{l-1})
     int cur = 0;
     for (int l = 4; l >= 1 && r == QLA_OK; --l) {
         r = conv(s, HID, HID, s->dz[cur], s->wb[l], nullptr, QLA_EPI_DGRAD, s->da[cur], s->z[l - 1], s->da[cur ^ 1],
                  s->dz[cur ^ 1], 1.0f, st);
-        if (r == QLA_OK) r = wgrad<HID, HID>(s, l, s->act[l - 1], s->dz[cur], st);
+        if (r == QLA_OK) r = wgrad(s, l, s->act[l - 1], HID, s->dz[cur], HID, st);
         cur ^= 1;
     }
-    if (r == QLA_OK) r = wgrad<X0C, HID>(s, 0, s->x0, s->dz[cur], st);
+    if (r == QLA_OK) r = wgrad(s, 0, s->x0, X0C, s->dz[cur], HID, st);
     return r;
 }
 
@@ -523,8 +487,8 @@ qla_status qla_surrogate_create(const qla_surrogate_config *cfg, qla_surrogate *
     for (int k = 0; k < 2; ++k) add(train ? NP * HID * 2 : 0);                                   // dz
     add(train ? NP * 16 * 4 : 0);                                                                // fout
     for (int k = 0; k < 2; ++k) add(train ? NP * HID * 4 : 0);                                   // da
-    add(train ? size_t(WSPLIT) * 9 * HID * HID * 4 : 0);                                         // wpart
-    add(train ? size_t(WSPLIT) * HID * 4 : 0);                                                   // bpart
+    add(train ? size_t(s->sms) * 9 * HID * HID * 4 : 0);                                         // wpart (per CTA)
+    add(train ? size_t(BIAS_BLOCKS) * HID * 4 : 0);                                              // bpart
     add(RED_BLOCKS * 8);                                                                         // red
     add(4 * 8);                                                                                  // scal
     add(sizeof(int));                                                                            // err

@@ -74,8 +74,13 @@ def generate(workloads: List[media.Workload], K: int = 16, snapshots: Optional[i
 
 
 def train(sur: Surrogate, data: Dict, iters: int, lr: float = 1e-3, lr_min: float = 1e-5, warmup: int = 50,
-          seed: int = 0, log_every: int = 100, time_limit: Optional[float] = None) -> List:
-    """Adam steps on random batches of consecutive-snapshot pairs. Returns [(iter, loss)]."""
+          seed: int = 0, log_every: int = 100, time_limit: Optional[float] = None, noise: float = 0.0) -> List:
+    """Adam steps on random batches of consecutive-snapshot pairs. Returns [(iter, loss)].
+
+    noise > 0 perturbs each input state by Gaussian noise of that standard
+    deviation relative to the batch RMS, keeping the target: the network then
+    also learns to pull a slightly wrong state back toward the trajectory,
+    which is what it meets in a rollout."""
     import torch
 
     q, nf = data["q"], data["n"]
@@ -86,6 +91,8 @@ def train(sur: Surrogate, data: Dict, iters: int, lr: float = 1e-3, lr_min: floa
     q_t = torch.empty_like(q_in)
     nb = torch.empty((B,) + tuple(nf.shape[1:]), dtype=torch.float32, device="cuda")
     hist = []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
     t0 = time.perf_counter()
     for it in range(iters):
         ti = torch.as_tensor(rng.integers(0, n_traj, B), device="cuda")
@@ -93,6 +100,9 @@ def train(sur: Surrogate, data: Dict, iters: int, lr: float = 1e-3, lr_min: floa
         q_in.copy_(q[ti, tj])
         q_t.copy_(q[ti, tj + 1])
         nb.copy_(nf[ti])
+        if noise > 0.0:
+            rms = q_in.square().mean().sqrt()
+            q_in.add_(torch.randn(q_in.shape, device="cuda", generator=gen) * (noise * rms))
         if it < warmup:
             lr_it = lr * (it + 1) / warmup
         else:
@@ -145,7 +155,7 @@ def evaluate(sur: Surrogate, w: media.Workload, calls: int, drift_tol: float = 1
             qs = sim.get_fields(np.float32).astype(np.float64)
             rel = float(np.linalg.norm(qs - qr) / np.linalg.norm(qr))
             persist = float(np.linalg.norm(q0 - qr) / np.linalg.norm(qr))
-            out["curve"].append({"steps": done * K, "rel_l2": rel, "rel_l2_no_update": persist,
+            out["curve"].append({"steps": done * K, "rollout_seconds": t_sur, "rel_l2": rel, "rel_l2_no_update": persist,
                                  "energy_drift": abs(sim.energy() / e_ref - 1.0),
                                  "qla_energy_drift": abs(ref.energy() / e_ref - 1.0),
                                  "fallbacks": stats_tot["fallback_calls"]})
@@ -155,14 +165,13 @@ def evaluate(sur: Surrogate, w: media.Workload, calls: int, drift_tol: float = 1
         out["energy_drift"] = out["curve"][-1]["energy_drift"]
         out["qla_energy_drift"] = out["curve"][-1]["qla_energy_drift"]
         out["rollout_seconds"] = t_sur
-        # device time of plain QLA for the same number of steps
+        # wall time of plain QLA for the same number of steps (as the rollout's)
         ref.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(ref.stream)
+        t0 = time.perf_counter()
         ref.step(calls * K)
-        e1.record(ref.stream)
-        e1.synchronize()
-        out["qla_seconds"] = e0.elapsed_time(e1) / 1e3
+        ref.synchronize()
+        out["qla_seconds"] = time.perf_counter() - t0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # device time of the network alone (one call)
         qa = torch.as_tensor(qr, dtype=torch.float32, device="cuda")
         qb = torch.empty_like(qa)
@@ -177,4 +186,74 @@ def evaluate(sur: Surrogate, w: media.Workload, calls: int, drift_tol: float = 1
     out["qla_seconds_per_K"] = out["qla_seconds"] / calls
     out["speedup_rollout"] = out["qla_seconds"] / t_sur
     out["speedup_forward"] = out["qla_seconds_per_K"] / out["forward_seconds_per_call"]
+    # horizon within the error bound, and the rollout's speedup over it
+    tol = 1e-2
+    horizon = 0
+    for c in out["curve"]:
+        if c["rel_l2"] > tol:
+            break
+        horizon = c["steps"]
+    out["horizon_steps_rel_l2_1e-2"] = horizon
+    if horizon:
+        t_h = [c["rollout_seconds"] for c in out["curve"] if c["steps"] == horizon][0]
+        out["speedup_at_rel_l2_1e-2"] = out["qla_seconds_per_K"] * (horizon // K) / t_h
+    else:
+        out["speedup_at_rel_l2_1e-2"] = None
     return out
+
+
+def save_checkpoint(path: str, params, meta: Dict) -> None:
+    import json
+
+    np.savez_compressed(path, params=np.asarray(params, dtype=np.float32), meta=json.dumps(meta))
+
+
+def load_checkpoint(path: str):
+    import json
+
+    z = np.load(path, allow_pickle=False)
+    return z["params"], json.loads(str(z["meta"]))
+
+
+def main(argv=None):
+    """Generate plain-QLA trajectories, train the surrogate on the GPU and save a checkpoint."""
+    import argparse
+    import json
+
+    import torch
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--trajectories", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=1024, help="QLA steps per trajectory")
+    ap.add_argument("--nx", type=int, default=512)
+    ap.add_argument("--ny", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--noise", type=float, default=0.0)
+    ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--init", default=None, help="start from this checkpoint")
+    a = ap.parse_args(argv)
+    K = 16
+    rng = np.random.default_rng(a.seed)
+    t0 = time.perf_counter()
+    wl = [training_workload(rng, a.nx, a.ny, 0.05, a.steps) for _ in range(a.trajectories)]
+    data = generate(wl, K)
+    t1 = time.perf_counter()
+    with Surrogate(a.ny, a.nx, nimg=a.batch, K=K, train=True, seed=a.seed) as sur:
+        if a.init:
+            sur.set_params(load_checkpoint(a.init)[0])
+        hist = train(sur, data, a.iters, lr=a.lr, log_every=max(1, a.iters // 40), seed=a.seed, noise=a.noise)
+        params = sur.get_params()
+    t2 = time.perf_counter()
+    meta = {"K": K, "out_scale": 1.0 / 16, "trajectories": a.trajectories, "steps": a.steps, "lattice": [a.nx, a.ny],
+            "delta": 0.05, "iters": a.iters, "batch": a.batch, "lr": a.lr, "noise": a.noise, "seed": a.seed,
+            "init": a.init, "final_loss": hist[-1][1], "data_seconds": t1 - t0, "train_seconds": t2 - t1,
+            "gpu": torch.cuda.get_device_name()}
+    save_checkpoint(a.out, params, meta)
+    print(json.dumps({"meta": meta, "loss": hist}))
+
+
+if __name__ == "__main__":
+    main()

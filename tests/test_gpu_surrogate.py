@@ -86,8 +86,9 @@ def run_grad(p, q, n, qt):
     return loss, g
 
 
-def test_gradients_match_oracle():
-    nimg, H, W = 2, 8, 128
+@pytest.mark.parametrize("nimg,H,W", [(2, 8, 128), (1, 1024, 128)])
+def test_gradients_match_oracle(nimg, H, W):
+    """Small case: one row per CTA; tall case: long runs of rows per CTA."""
     p = random_params(3)
     q, n = make_inputs(nimg, H, W, 4)
     rng = np.random.default_rng(5)
