@@ -13,6 +13,7 @@ the same lattice, relative L2 error, energy drift and time per K steps.
 from __future__ import annotations
 
 import math
+import os
 import time
 from typing import Dict, List, Optional
 
@@ -200,6 +201,9 @@ def evaluate(sur: Surrogate, w: media.Workload, calls: int, drift_tol: float = 1
     else:
         out["speedup_at_rel_l2_1e-2"] = None
     return out
+
+
+DEFAULT_CHECKPOINT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "checkpoints", "surrogate_k16.npz")
 
 
 def save_checkpoint(path: str, params, meta: Dict) -> None:

@@ -175,3 +175,43 @@ def test_surrogate_rejects_bad_arguments():
         bad[5] = np.nan
         with pytest.raises(QLAError):
             sur.set_params(bad)
+
+
+def test_trained_checkpoint_gains_over_the_method_without_it():
+    """The committed checkpoint against no update (Q_{t+K} = Q_t) and against
+    the same network untrained, on a held-out lattice (raw network error: no
+    energy check)."""
+    from paper_2301_13601_gb300 import surrogate_train as T
+
+    params, meta = T.load_checkpoint(T.DEFAULT_CHECKPOINT)
+    w = T.training_workload(np.random.default_rng(999), 512, 256, 0.05, 512)
+    with S.Surrogate(256, 512, K=meta["K"], out_scale=meta["out_scale"]) as sur:
+        sur.set_params(params)
+        tr = T.evaluate(sur, w, 32, drift_tol=1e30, checkpoints=4)
+        sur.init_params(1)
+        un = T.evaluate(sur, w, 32, drift_tol=1e30, checkpoints=4)
+    print("trained", tr["rel_l2"], "no update", tr["rel_l2_no_update"], "untrained", un["rel_l2"])
+    assert tr["fallback_calls"] == 0 and tr["surrogate_calls"] == 32
+    assert tr["rel_l2"] < 0.05 * tr["rel_l2_no_update"]
+    assert tr["rel_l2"] < 0.05 * un["rel_l2"]
+    assert tr["rel_l2"] < 1e-2  # 512 steps within the error bound
+
+
+def test_short_training_from_scratch_improves_held_out_error():
+    """Train on the GPU from random weights for a few hundred steps: the
+    held-out error drops well below the untrained network's."""
+    from paper_2301_13601_gb300 import surrogate_train as T
+
+    rng = np.random.default_rng(5)
+    data = T.generate([T.training_workload(rng, 512, 256, 0.05, 256) for _ in range(8)], 16)
+    w = T.training_workload(np.random.default_rng(998), 512, 256, 0.05, 256)
+    with S.Surrogate(256, 512, nimg=4, train=True, seed=3) as sur:
+        with S.Surrogate(256, 512) as inf:
+            inf.set_params(sur.get_params())
+            before = T.evaluate(inf, w, 8, drift_tol=1e30)["rel_l2"]
+            hist = T.train(sur, data, 400, lr=1e-3, log_every=100)
+            inf.set_params(sur.get_params())
+            after = T.evaluate(inf, w, 8, drift_tol=1e30)["rel_l2"]
+    print("loss", hist, "held-out rel L2 before", before, "after", after)
+    assert hist[-1][1] < 0.3 * hist[1][1]
+    assert after < before / 3
