@@ -354,6 +354,76 @@ def surrogate_report(calls: int = 250, seed: int = 7):
     }
 
 
+def run_surrogate(args):
+    """The surrogate alone on the 1024^2 workload: forward calls (16 QLA steps
+    each) on device-resident fields, and training steps (batch 4 of 512x256),
+    timed with CUDA events; the conv kernel's throughput against the BF16 peak."""
+    import numpy as np
+    import torch
+
+    from paper_2301_13601_gb300 import build as _build
+    from paper_2301_13601_gb300 import media
+    from paper_2301_13601_gb300 import surrogate as S
+    from paper_2301_13601_gb300 import surrogate_train as T
+
+    _build.build()
+    params, meta = T.load_checkpoint(SURROGATE_CHECKPOINT)
+    w = media.workload_surrogate_1024(7)
+    n = torch.as_tensor(np.stack(w.medium()), dtype=torch.float32, device="cuda")[None].contiguous()
+    q = [torch.randn((1, 6, w.Ny, w.Nx), device="cuda") * 0.5 for _ in range(2)]
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    with S.Surrogate(w.Ny, w.Nx, K=meta["K"], out_scale=meta["out_scale"]) as sur:
+        sur.set_params(params)
+        for i in range(args.warmup):
+            sur.forward(q[i & 1], n, q[(i + 1) & 1])
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(sur.stream)
+        for i in range(args.steps):
+            sur.forward(q[i & 1], n, q[(i + 1) & 1])
+        e1.record(sur.stream)
+        e1.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / args.steps
+        flops = sur.info()["flops_per_call"]
+    with S.Surrogate(256, 512, nimg=4, K=meta["K"], out_scale=meta["out_scale"], train=True) as tr:
+        tr.set_params(params)
+        qa = torch.randn((4, 6, 256, 512), device="cuda")
+        na = torch.rand((4, 3, 256, 512), device="cuda") * 2 + 1
+        qb = qa * 1.01
+        for _ in range(args.warmup):
+            tr.train_step(qa, na, qb, 1e-6)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(tr.stream)
+        for _ in range(args.steps):
+            tr.train_step(qa, na, qb, 1e-6)
+        e1.record(tr.stream)
+        e1.synchronize()
+        train_ms = e0.elapsed_time(e1) / args.steps
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    achieved = flops / (fwd_ms / 1e3) / 1e12
+    sites = w.Nx * w.Ny
+    line = {"metric": "QLA-equivalent site-updates/s of the surrogate forward", "value": sites * 16 / (fwd_ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic", "config": {"workload": "surrogate1024 seed 7", "lattice": "1024x1024",
+                                            "steps_per_call": 16, "l2": "activations 128 MB per buffer"},
+            "training_step_ms": train_ms, "training_batch": "4 x 512x256",
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": achieved / bf16, "kernel": "conv3x3_tc_kernel (6 layers per call)",
+                         "peak_kind": "measured" if peaks.get("bf16_tflops") else "fallback"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """64 lattices of uneven sizes in one persistent graph launch per bench step."""
     import torch
@@ -400,7 +470,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["cylinders8192", "ellipse2048", "cylinder256", "batch64"],
+    ap.add_argument("--workload", choices=["cylinders8192", "ellipse2048", "cylinder256", "batch64", "surrogate1024"],
                     default="cylinders8192")
     ap.add_argument("--batch-step-scale", type=int, default=10, help="batch64: steps of each lattice divided by this")
     ap.add_argument("--chunk-rows", type=int, default=0)
@@ -413,6 +483,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "surrogate1024":
+        run_surrogate(args)
     else:
         run_ours(args)
 

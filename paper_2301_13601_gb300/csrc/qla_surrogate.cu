@@ -172,7 +172,8 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int S, const
     const int total = nout * cin * 9;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < total) {
-        const int t = i % 9, c = (i / 9) % cin, n = i / (9 * cin);
+        // c fastest: consecutive threads read consecutive partials
+        const int c = i % cin, n = (i / cin) % nout, t = i / (cin * nout);
         const int c1 = tied ? (c < 6 ? c : c + 6) : c;
         const int c2 = (tied && c < 6) ? c + 6 : -1;
         float acc = 0.0f;
@@ -181,7 +182,7 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int S, const
             acc += o[c1];
             if (c2 >= 0) acc += o[c2];
         }
-        gw[i] = acc;
+        gw[(n * cin + c) * 9 + t] = acc;
     } else if (i < total + nout) {
         const int n = i - total;
         float acc = 0.0f;
