@@ -110,6 +110,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
 
 
+def job_throughput(units: float, elapsed_ms: float, world: int, device=None):
+    """Whole-job throughput over ranks: units summed over ranks divided by the
+    slowest rank's elapsed time (the job ends when its last rank does).
+    Returns (units per second, max elapsed ms). world == 1 needs no process group."""
+    if world == 1:
+        return units / (elapsed_ms / 1e3), elapsed_ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) / 1e3), float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -233,13 +249,9 @@ def run_ours(args):
     clocks.stop()
     total_ms = e_begin.elapsed_time(e_end)
     sweep_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([total_ms], device="cuda")
+    value, total_ms = job_throughput(sites * S * args.steps, total_ms, world, device="cuda")
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    total_ms = float(t.item())
-    site_updates = sites * S * args.steps * world
-    value = site_updates / (total_ms / 1e3)
     launches_per_step = math.ceil(S / sim.steps_per_pass)
     # e2e through the public API with host buffers: pinned H2D state copy,
     # qla_step, diagnostics, D2H state copy, every bench step

@@ -131,8 +131,9 @@ enum {
 };
 
 /* Advance an FP32 QLA context by `calls` x K steps with the network. After each
- * call the energy (Eq. 27, mean of Q.Q) of the proposed state is computed in
- * FP64; if it is non-finite or its drift (drift_mode) exceeds drift_tol, the
+ * call the energy (Eq. 27, mean of Q.Q) of the proposed state is computed
+ * (FP32 squares, FP64 sums: ~1e-6 relative); if it is non-finite or its drift
+ * (drift_mode) exceeds drift_tol, the
  * proposal is discarded and K plain QLA steps (qla_step) are taken from the
  * unchanged state instead. With QLA_DRIFT_FROM_START, energy_ref > 0 sets
  * E_ref (e.g. the energy at the start of an earlier rollout segment);

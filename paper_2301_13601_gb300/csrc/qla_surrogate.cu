@@ -99,6 +99,18 @@ __global__ void dq_sumsq_kernel(const float *__restrict__ qt, const float *__res
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// part[b] = sum over this block's elements of q^2: FP32 squares summed per
+// thread (a few dozen terms), FP64 across threads and blocks. Accurate to
+// ~1e-6 relative, ample for a drift check at 1e-3; a non-finite element makes
+// the sum non-finite.
+__global__ void sumsq_kernel(const float *__restrict__ q, long long n, double *__restrict__ part) {
+    float acc = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc = fmaf(q[i], q[i], acc);
+    const double s = block_sum(double(acc));
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void finalize_kernel(const double *__restrict__ part, int nb, double *__restrict__ out) {
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
@@ -233,9 +245,6 @@ struct qla_surrogate {
     float *wpart = nullptr, *bpart = nullptr;
     double *red = nullptr, *scal = nullptr;  // scal[0] = sum dQ^2, scal[1] = sum residual^2
     int *err = nullptr;
-    void *dscratch = nullptr;
-    DiagResult *ddev = nullptr;
-    DiagResult *dhost = nullptr;  // pinned
     double *host_scal = nullptr;  // pinned [2]
     int *host_err = nullptr;      // pinned
     bool packed = false;
@@ -493,8 +502,6 @@ qla_status qla_surrogate_create(const qla_surrogate_config *cfg, qla_surrogate *
     add(RED_BLOCKS * 8);                                                                         // red
     add(4 * 8);                                                                                  // scal
     add(sizeof(int));                                                                            // err
-    add(diag_scratch_bytes(c.W, c.H));                                                           // dscratch
-    add(sizeof(DiagResult));                                                                     // ddev
     size_t total = 0;
     for (size_t b : sizes) total += b;
     if (cudaMalloc(&s->arena, total) != cudaSuccess) {
@@ -528,10 +535,7 @@ qla_status qla_surrogate_create(const qla_surrogate_config *cfg, qla_surrogate *
     s->red = static_cast<double *>(take());
     s->scal = static_cast<double *>(take());
     s->err = static_cast<int *>(take());
-    s->dscratch = take();
-    s->ddev = static_cast<DiagResult *>(take());
-    if (cudaMallocHost(&s->dhost, sizeof(DiagResult)) != cudaSuccess ||
-        cudaMallocHost(&s->host_scal, 4 * sizeof(double)) != cudaSuccess ||
+    if (cudaMallocHost(&s->host_scal, 4 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&s->host_err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         qla_surrogate_destroy(s);
@@ -662,14 +666,19 @@ qla_status qla_surrogate_rollout(qla_surrogate *s, qla_ctx *ctx, const float *n,
         r = repack(s, v.stream);
         if (r != QLA_OK) return r;
     }
+    // Eq. 27 energy (mean over sites of Q.Q) of a proposal or state: one light
+    // reduction (the full diagnostics add div B and compensated FP64 sums,
+    // which the drift check does not need and which cost more than the check).
     auto energy = [&](const void *q, double *e, bool *finite) -> qla_status {
-        SG_CUDA(s, launch_diagnostics(q, 0, v.Nx, v.Ny, s->dscratch, s->ddev, v.stream));
-        SG_CUDA(s, cudaMemcpyAsync(s->dhost, s->ddev, sizeof(DiagResult), cudaMemcpyDeviceToHost, v.stream));
+        sumsq_kernel<<<RED_BLOCKS, 256, 0, v.stream>>>(static_cast<const float *>(q), 6LL * v.Nx * v.Ny, s->red);
+        finalize_kernel<<<1, 256, 0, v.stream>>>(s->red, RED_BLOCKS, s->scal + 2);
+        SG_CUDA(s, cudaGetLastError());
+        SG_CUDA(s, cudaMemcpyAsync(s->host_scal + 2, s->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, v.stream));
         SG_CUDA(s, cudaMemcpyAsync(s->host_err, s->err, sizeof(int), cudaMemcpyDeviceToHost, v.stream));
         SG_CUDA(s, cudaStreamSynchronize(v.stream));
         if (*s->host_err) return sfail(s, QLA_ETIMEOUT, "rollout: a tensor-core wait ran out of its limit");
-        *e = s->dhost->energy_sum / (double(v.Nx) * v.Ny);
-        *finite = s->dhost->nonfinite == 0;
+        *e = s->host_scal[2] / (double(v.Nx) * v.Ny);
+        *finite = isfinite(*e) != 0;
         return QLA_OK;
     };
     qla_rollout_stats st{};
@@ -730,7 +739,6 @@ void qla_surrogate_destroy(qla_surrogate *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->arena) cudaFree(s->arena);
-    if (s->dhost) cudaFreeHost(s->dhost);
     if (s->host_scal) cudaFreeHost(s->host_scal);
     if (s->host_err) cudaFreeHost(s->host_err);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
