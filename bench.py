@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # on the default workload; valid only for the kernel source it was measured on
 # (profiles/sweep_kernel_cylinders8192_launches.md).
 MEASURED_TRAFFIC = {"sweep_sha256_prefix": "0fb407d32f29a1d4", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 4, "bytes_per_launch": 5.536e9 + 1.592e9}
+                    "steps_per_pass": 4, "chunk_rows": 1024, "bytes_per_launch": 5.849e9 + 1.595e9}
 
 METRIC = "site-updates/s per QLA step"
 UNIT = "site-updates/s"
@@ -281,7 +281,7 @@ def run_ours(args):
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     traffic = None
     if (sha == MEASURED_TRAFFIC["sweep_sha256_prefix"] and w.name == MEASURED_TRAFFIC["workload"]
-            and k == MEASURED_TRAFFIC["steps_per_pass"]):
+            and k == MEASURED_TRAFFIC["steps_per_pass"] and sim.chunk_rows == MEASURED_TRAFFIC["chunk_rows"]):
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     launch_ms = sweep_ms / (args.steps * launches_per_step)
     achieved = BYTES_PER_SITE_UPDATE * sites * k / (launch_ms / 1e3) / 1e9

@@ -97,6 +97,12 @@ int sm_count(int dev) {
 
 // Rows per tile: choose the number of row chunks that minimises
 // (waves of CTAs) x (rows swept per CTA, warm-up included).
+// Rows per tile: the fewest waves x (rows + warm-up rows) among tiles of at
+// most kMaxAutoChunk rows. The cap is measured, not modelled: on the 8192^2
+// workload (K = 4) tiles of 512-1280 rows run 39-40 G site-updates/s against
+// 36 G for the single-wave 4096-row split the wave model alone prefers.
+constexpr int kMaxAutoChunk = 1024;
+
 int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
     const int W = qla::sweep_strip_width();
     const int wv = W - 8 * K;
@@ -104,11 +110,12 @@ int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
     const int occ = prec ? qla::sweep_occupancy_f64(K, 1) : qla::sweep_occupancy_f32(K, 1);
     const long long slots = (long long)sms * occ;
     double best = 1e300;
-    int best_chunk = Ny;
+    int best_chunk = std::min(Ny, kMaxAutoChunk);
     for (int ncy = 1; ncy <= std::max(1, Ny / 8); ++ncy) {
         int ch = (Ny + ncy - 1) / ncy;
         ch = (ch + 7) / 8 * 8;
         if (ch > Ny) ch = Ny;
+        if (ch > kMaxAutoChunk) continue;
         const int real_ncy = (Ny + ch - 1) / ch;
         const long long ctas = (long long)nsx * real_ncy * 2;
         const long long waves = (ctas + slots - 1) / slots;
@@ -117,7 +124,7 @@ int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
             best = cost;
             best_chunk = ch;
         }
-        if (ctas > 64 * slots) break;
+        if (ctas > 64 * slots && best < 1e300) break;
     }
     return std::max(1, best_chunk);
 }
