@@ -5,8 +5,9 @@
 //   f  = conv5(a4)   (3x3 circular convolutions, 64 hidden channels).
 // The forward and input-gradient convolutions run on the tcgen05 tensor cores
 // (qla_conv.cu), and so do the weight gradients (pixels as the reduction
-// dimension, per-CTA partial sums reduced in a fixed order); the optimiser is Adam on FP32 master weights that are re-packed to
-// BF16 after every update. The input x0 carries each field as two BF16 parts
+// dimension, per-CTA partial sums reduced in a fixed order); the optimiser
+// is Adam on FP32 master weights that are re-packed to BF16 after every
+// update. The input x0 carries each field as two BF16 parts
 // (high and low) that share first-layer weights, so the network sees the
 // FP32 state to about 16 significant bits, plus n in BF16.
 //

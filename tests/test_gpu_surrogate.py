@@ -215,3 +215,57 @@ def test_short_training_from_scratch_improves_held_out_error():
     print("loss", hist, "held-out rel L2 before", before, "after", after)
     assert hist[-1][1] < 0.3 * hist[1][1]
     assert after < before / 3
+
+
+def test_batched_forward_equals_single_image_forwards():
+    """Images of a batch are independent (each periodic on its own): bit-identical to one-image calls."""
+    H, W = 16, 256
+    q, n = make_inputs(2, H, W, 20)
+    p = random_params(21)
+    with S.Surrogate(H, W, nimg=2) as b2, S.Surrogate(H, W) as b1:
+        b2.set_params(p)
+        b1.set_params(p)
+        qi = torch.as_tensor(q, device=dev)
+        ni = torch.as_tensor(n, device=dev)
+        out2 = torch.empty_like(qi)
+        b2.forward(qi, ni, out2)
+        singles = []
+        for i in range(2):
+            o = torch.empty_like(qi[i:i + 1])
+            b1.forward(qi[i:i + 1].contiguous(), ni[i:i + 1].contiguous(), o)
+            singles.append(o)
+        torch.cuda.synchronize()
+    assert torch.equal(out2, torch.cat(singles))
+
+
+def test_params_round_trip_and_count():
+    p = random_params(30)
+    with S.Surrogate(8, 128) as sur:
+        sur.set_params(p)
+        assert np.array_equal(sur.get_params(), p)
+        info = sur.info()
+    assert info["params"] == p.size
+    assert info["flops_per_call"] == 2 * 8 * 128 * 9 * (16 * 64 + 4 * 64 * 64 + 64 * 16)
+
+
+def test_rollout_drift_from_start_mode():
+    """With a fixed energy reference, a tolerance of 0 rejects every proposal
+    and an infinite one accepts all; the lattice must match the surrogate's."""
+    from paper_2301_13601_gb300 import media
+    from paper_2301_13601_gb300.qla import QLAError, Simulation
+
+    Nx, Ny = 128, 32
+    nfield = media.medium(Nx, Ny, [])
+    nf = torch.as_tensor(np.stack(nfield), dtype=torch.float32, device=dev)
+    with S.Surrogate(Ny, Nx, K=16, seed=11) as sur, Simulation(*nfield, 0.05) as sim:
+        sim.init_pulse("Ey", 60, 8)
+        e0 = sim.energy()
+        st = sur.rollout(sim, nf, 2, drift_tol=0.0, drift_mode=S.DRIFT_FROM_START, energy_ref=e0)
+        assert st["fallback_calls"] == 2 and abs(st["energy_ref"] / e0 - 1) < 1e-15
+        st = sur.rollout(sim, nf, 2, drift_tol=1e30, drift_mode=S.DRIFT_FROM_START)
+        assert st["surrogate_calls"] == 2
+        assert st["energy_ref"] > 0.0  # measured on the state at the start of this rollout
+    with S.Surrogate(Ny, 256, K=16, seed=11) as sur, Simulation(*nfield, 0.05) as sim:
+        sim.init_pulse("Ey", 60, 8)
+        with pytest.raises(QLAError):
+            sur.rollout(sim, nf, 1)
