@@ -27,8 +27,9 @@
 //  * No compute phase touches global memory for its inputs: the y-pass
 //    coefficients of an iteration are copied into shared memory with cp.async
 //    while the x-pass of that iteration runs, and the x-pass coefficients and
-//    next level-0 rows while the y-pass of the previous iteration runs. Rows
-//    are bulk-prefetched into L2 two iterations ahead.
+//    next level-0 rows while the y-pass of the previous iteration runs. (A
+//    bulk L2 prefetch two iterations ahead was measured to cost 18% on top of
+//    this staging and is not used.)
 //  * Rotations use the (cos-1, sin) form h' = h + (m h + s p): one rounding at
 //    the scale of h per output, with coefficients whose FP32 norm error is
 //    minimised at creation. Coefficients are stored as (m, s) pairs.
@@ -236,10 +237,6 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-// Hint: bring [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte aligned).
-__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
-}
 
 // Copies the strip's 256 columns of one global row into a (swizzled) shared
 // row: lane l copies strip columns 8l .. 8l+7. xb: wrapped global column of
@@ -390,33 +387,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             copy_strip_row(ystrow(j, slot, ir), plane + size_t(growof(j, it, ir)) * Nx, xb, Nx, nowrap, vec, lane);
         }
     };
-    // L2 prefetch of the level-0 rows of iteration it (state and coefficients)
-    auto prefetch_rows = [&](int it) {
-        constexpr int NPL = 3 + 4;
-        if (!vec || (xb & 1)) return;
-        for (int task = tid; task < R * NPL; task += NT) {
-            const int ir = task / NPL, k = task % NPL;
-            const int row = growof(0, it, ir);
-            const char *rowp;
-            int esz;
-            if (k < 3) {
-                rowp = reinterpret_cast<const char *>((k == 0 ? qh : (k == 1 ? qpx : qpy)) + size_t(row) * Nx);
-                esz = sizeof(T);
-            } else {
-                const T2 *pl = k == 3 ? pCX : (k == 4 ? pCY : (k == 5 ? pVX : pVY));
-                if (k == 4 && Fm::CX == Fm::CY) continue;
-                rowp = reinterpret_cast<const char *>(pl + size_t(row) * Nx);
-                esz = sizeof(T2);
-            }
-            if (W_IN >= Nx) {
-                prefetch_l2(rowp, unsigned(Nx * esz));
-            } else {
-                const int len1 = min(W_IN, Nx - xb);
-                prefetch_l2(rowp + size_t(xb) * esz, unsigned(len1 * esz));
-                if (len1 < W_IN) prefetch_l2(rowp, unsigned((W_IN - len1) * esz));
-            }
-        }
-    };
 
     for (int i = tid; i < int(L::STATE / sizeof(T)); i += NT) buf[i] = T(0);
 
@@ -445,8 +415,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     T *const qo_py = qout + size_t(Fm::PY) * P + gx;
 
     __syncthreads();  // zeroed buffers before the async copies land
-    prefetch_rows(0);
-    prefetch_rows(1);
     copy_state0(0, 0);
     copy_xstash(0);
     cp_async_commit();
@@ -459,7 +427,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
 
     for (int it = 0; it < nit; ++it) {
         const int cur = it & 1;
-        prefetch_rows(it + 2);
         copy_ystash(it);
         cp_async_commit();
 
