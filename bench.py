@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 # DRAM bytes per sweep launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on the default workload; valid only for the kernel source it was measured on
 # (profiles/sweep_kernel_cylinders8192_launches.md).
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "0fb407d32f29a1d4", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 4, "chunk_rows": 1024, "bytes_per_launch": 5.849e9 + 1.595e9}
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "35a058aae99d0f8b", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 4, "chunk_rows": 1024, "bytes_per_launch": 5.701e9 + 1.593e9}
 
 METRIC = "site-updates/s per QLA step"
 UNIT = "site-updates/s"

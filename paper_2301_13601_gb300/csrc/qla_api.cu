@@ -27,6 +27,8 @@ struct qla_ctx {
     void *scratch = nullptr;
     qla::DiagResult *diag_dev = nullptr;
     qla::DiagResult *diag_host = nullptr;
+    int *sweep_err = nullptr;       // device flag: a bounded wait of the sweep's TMA copies ran out
+    int *sweep_err_host = nullptr;  // pinned
     size_t esize = 4;
     int K = 4;
     int chunk = 0;
@@ -142,10 +144,19 @@ qla_status launch_pass(qla_ctx *c, int K) {
     a.unitary = c->opt.potential == QLA_POT_UNITARY ? 1 : 0;
     a.vec = (c->Nx % int(16 / c->esize)) == 0 ? 1 : 0;
     a.fam0 = 0;
+    a.error = c->sweep_err;
     cudaError_t e = c->opt.precision == QLA_FP64 ? qla::launch_sweep_f64(K, a, 2, c->stream)
                                                   : qla::launch_sweep_f32(K, a, 2, c->stream);
     if (e != cudaSuccess) return fail(c, QLA_ECUDA, "sweep launch (K=%d): %s", K, cudaGetErrorString(e));
     c->cur ^= 1;
+    return QLA_OK;
+}
+
+// After a stream synchronisation: report a sweep whose TMA copy wait ran out.
+qla_status check_sweep_error(qla_ctx *c) {
+    QLA_CUDA(c, cudaMemcpyAsync(c->sweep_err_host, c->sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (*c->sweep_err_host) return fail(c, QLA_ETIMEOUT, "a sweep's wait for its row copies ran out of its limit");
     return QLA_OK;
 }
 
@@ -158,8 +169,7 @@ qla_status run_diag(qla_ctx *c) {
     if (e != cudaSuccess) return fail(c, QLA_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
     QLA_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_dev, sizeof(qla::DiagResult), cudaMemcpyDeviceToHost,
                                 c->stream));
-    QLA_CUDA(c, cudaStreamSynchronize(c->stream));
-    return QLA_OK;
+    return check_sweep_error(c);
 }
 
 }  // namespace
@@ -187,7 +197,8 @@ qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_bu
     out->state_bytes = round_up(6 * P * es, kAlign);
     out->coeff_bytes = round_up(size_t(qla::NCOEF) * P * es, kAlign);
     out->index_bytes = round_up(3 * P * sizeof(double), kAlign);
-    out->scratch_bytes = round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign) + round_up(sizeof(qla::DiagResult), kAlign);
+    out->scratch_bytes = round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign) + round_up(sizeof(qla::DiagResult), kAlign) +
+                         kAlign;  // sweep error flag
     return QLA_OK;
 }
 
@@ -259,8 +270,12 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
     }
     c->diag_dev = reinterpret_cast<qla::DiagResult *>(static_cast<char *>(c->scratch) +
                                                       round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign));
-    if (cudaMallocHost(reinterpret_cast<void **>(&c->diag_host), sizeof(qla::DiagResult)) != cudaSuccess)
+    c->sweep_err = reinterpret_cast<int *>(reinterpret_cast<char *>(c->diag_dev) +
+                                           round_up(sizeof(qla::DiagResult), kAlign));
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->diag_host), sizeof(qla::DiagResult)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&c->sweep_err_host), sizeof(int)) != cudaSuccess)
         return bail(QLA_ENOMEM);
+    if (cudaMemsetAsync(c->sweep_err, 0, sizeof(int), c->stream) != cudaSuccess) return bail(QLA_ECUDA);
     for (int k = 0; k < 3; ++k)
         if (cudaMemcpyAsync(c->index + size_t(k) * P, nn[k], P * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream) != cudaSuccess)
@@ -421,7 +436,7 @@ qla_status qla_synchronize(qla_ctx *c) {
     qla_status s = enter(c);
     if (s != QLA_OK) return s;
     QLA_CUDA(c, cudaStreamSynchronize(c->stream));
-    return QLA_OK;
+    return check_sweep_error(c);
 }
 
 long long qla_step_count(const qla_ctx *c) { return c ? c->steps : -1; }
@@ -462,6 +477,7 @@ void qla_destroy(qla_ctx *c) {
         cudaFree(c->scratch);
     }
     if (c->diag_host) cudaFreeHost(c->diag_host);
+    if (c->sweep_err_host) cudaFreeHost(c->sweep_err_host);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;

@@ -59,7 +59,7 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB)
     batch_kernel(const BatchSched S) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int sh[6];  // stop, instance, pass, family, strip, chunk
     for (;;) {
         if (threadIdx.x == 0) {
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
         a.unitary = UNIT ? 1 : 0;
         a.vec = I.vec;
         a.fam0 = 0;
+        a.error = nullptr;  // the batch copies with cp.async (no TMA waits)
         if (fam == 0) sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, chunk, smem_raw);
         else sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, chunk, smem_raw);
         __threadfence();

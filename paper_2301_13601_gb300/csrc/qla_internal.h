@@ -50,6 +50,7 @@ struct SweepArgs {
     int unitary;        // 1: unitary potentials
     int vec;            // 1: 16-byte vector access is legal (Nx multiple of 16/sizeof(T))
     int fam0;           // first family index handled by blockIdx.z = 0 (0 = TM, 1 = TE)
+    int *error;         // device flag set when a bounded wait of the TMA copy path runs out (null: no TMA)
 };
 
 // Sweep kernel launcher: one fused pass of K time steps over the lattice.

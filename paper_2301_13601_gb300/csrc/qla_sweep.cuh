@@ -35,9 +35,13 @@
 //    minimised at creation. Coefficients are stored as (m, s) pairs.
 #pragma once
 
+#include <cuda.h>
+#include <string.h>
+
 #include <type_traits>
 
 #include "qla_internal.h"
+#include "qla_tc.cuh"
 
 namespace qla {
 
@@ -46,6 +50,14 @@ constexpr int W_IN = 32 * LANE_COLS;
 
 struct SweepParams {
     SweepArgs a;
+    // Tensor maps for the TMA row loads (FP32, used when tma != 0): the input
+    // state viewed as [6][Ny][Nx/8][8] floats with the 32-byte swizzle and the
+    // coefficient pairs as [7][Ny][Nx/8][16] floats with the 64-byte swizzle.
+    // One box (8 x 32, resp. 16 x 32) is one 256-column strip row, landing in
+    // exactly the XOR-swizzled layout of the shared row buffers (swz below).
+    CUtensorMap tm_state;
+    CUtensorMap tm_coef;
+    int tma;
 };
 
 template <typename T>
@@ -238,6 +250,20 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// One strip row by TMA: the box at (0, c1, c2, c3) of `map` into `dst`,
+// completing `bytes` on the mbarrier.
+__device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *map, int c1, int c2, int c3, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(tc::smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
 // Copies the strip's 256 columns of one global row into a (swizzled) shared
 // row: lane l copies strip columns 8l .. 8l+7. xb: wrapped global column of
 // strip column 0; nowrap: the strip lies inside [0, Nx).
@@ -270,7 +296,8 @@ struct SweepLayout {
     static constexpr size_t STATE = size_t(K) * 2 * 3 * R * W_IN * sizeof(T);
     static constexpr size_t YST = size_t(K) * NYS * R * W_IN * sizeof(T2);
     static constexpr size_t XST = size_t(K) * NXS * R * W_IN * sizeof(T2);
-    static constexpr size_t SMEM = STATE + YST + XST;
+    static constexpr size_t BAR_OFF = STATE + YST + XST;  // two mbarriers of the TMA copy groups
+    static constexpr size_t SMEM = BAR_OFF + 64;
 };
 
 template <typename T, int K, int R, int NY>
@@ -302,7 +329,9 @@ struct YPipe {
 };
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
-__device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int chunk_idx, unsigned char *smem_raw) {
+__device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int chunk_idx, unsigned char *smem_raw,
+                                           const CUtensorMap *tm_state = nullptr,
+                                           const CUtensorMap *tm_coef = nullptr) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     using T2 = typename Ar<T>::T2;
@@ -388,6 +417,60 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         }
     };
 
+    // TMA path (FP32, a strip that does not wrap around x, 8-column aligned):
+    // warp 0 issues each copy group, one row per TMA load; lane 0 first posts
+    // the group's byte count on its mbarrier (group X: x-pass coefficients and
+    // level-0 state rows; group Y: y-pass coefficients), and every thread waits
+    // on the mbarrier where the cp.async path waits for its groups.
+    uint64_t *const tbar = reinterpret_cast<uint64_t *>(smem_raw + L::BAR_OFF);
+    bool use_tma = false;
+    if constexpr (std::is_same<T, float>::value)
+        use_tma = tm_state != nullptr && tm_coef != nullptr && nowrap && (xb & 7) == 0 &&
+                  (tc::smem_addr(smem_raw) & 1023u) == 0;
+    uint32_t tph_x = 0, tph_y = 0;
+    constexpr uint32_t SROW = W_IN * sizeof(T), CROW = W_IN * sizeof(T2);
+    auto tma_group_x = [&](int it, bool with_state, int half) {
+        if (warp != 0) return;
+        int nrows = 0;
+        for (int j = 0; j < K; ++j)
+            if (active(j, it)) nrows += NXS * R;
+        const uint32_t bytes = uint32_t(nrows) * CROW + (with_state ? 3u * R * SROW : 0u);
+        tc::fence_proxy_async();
+        if (lane == 0) mbar_arrive_expect_tx(&tbar[0], bytes);
+        __syncwarp();
+        for (int task = lane; task < K * NXS * R; task += 32) {
+            const int j = task / (NXS * R), rem = task % (NXS * R);
+            const int slot = rem / R, ir = rem % R;
+            if (!active(j, it)) continue;
+            tma_row(xstrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir), slot == 0 ? Fm::CX : Fm::VX, &tbar[0]);
+        }
+        if (with_state) {
+            for (int task = lane; task < 3 * R; task += 32) {
+                const int comp = task / R, ir = task % R;
+                tma_row(bufrow(0, half, comp, ir), tm_state, xb >> 3, growof(0, it, ir),
+                        comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[0]);
+            }
+        }
+    };
+    auto tma_group_y = [&](int it) {
+        if (warp != 0) return;
+        tc::fence_proxy_async();
+        if (lane == 0) mbar_arrive_expect_tx(&tbar[1], uint32_t(K * NYS * R) * CROW);
+        __syncwarp();
+        for (int task = lane; task < K * NYS * R; task += 32) {
+            const int j = task / (NYS * R), rem = task % (NYS * R);
+            const int slot = rem / R, ir = rem % R;
+            tma_row(ystrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir),
+                    slot == 0 ? Fm::CY : (slot == 1 ? Fm::VY : Fm::VX), &tbar[1]);
+        }
+    };
+    // bounded wait for a copy group; a timeout sets the error flag (the
+    // results of the launch are then invalid) instead of hanging
+    auto tma_wait = [&](int b, uint32_t &ph) {
+        if (!tc::mbar_wait(&tbar[b], ph, 1u << 24) && A.error) atomicExch(A.error, 1);
+        ph ^= 1u;
+    };
+
     for (int i = tid; i < int(L::STATE / sizeof(T)); i += NT) buf[i] = T(0);
 
     // ---- y-pass tasks: fixed (level, column) per thread slot ---------------
@@ -414,11 +497,25 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     T *const qo_px = qout + size_t(Fm::PX) * P + gx;
     T *const qo_py = qout + size_t(Fm::PY) * P + gx;
 
+    // generic writes and reads of shared memory are ordered before the TMA
+    // (async proxy) writes that later reuse the same rows: every thread fences
+    // before the barrier that precedes an issue
+    if (use_tma) tc::fence_proxy_async();
+    if (use_tma && tid == 0) {
+        tc::mbar_init(&tbar[0], 1);
+        tc::mbar_init(&tbar[1], 1);
+        tc::fence_mbar_init();
+    }
     __syncthreads();  // zeroed buffers before the async copies land
-    copy_state0(0, 0);
-    copy_xstash(0);
-    cp_async_commit();
-    cp_async_wait_all();
+    if (use_tma) {
+        tma_group_x(0, true, 0);
+        tma_wait(0, tph_x);
+    } else {
+        copy_state0(0, 0);
+        copy_xstash(0);
+        cp_async_commit();
+        cp_async_wait_all();
+    }
     __syncthreads();
 
     YPipe<T> yp[NY];
@@ -427,8 +524,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
 
     for (int it = 0; it < nit; ++it) {
         const int cur = it & 1;
-        copy_ystash(it);
-        cp_async_commit();
+        if (use_tma) {
+            tma_group_y(it);
+        } else {
+            copy_ystash(it);
+            cp_async_commit();
+        }
 
         // ---- phase 1: x-pass, one warp per (level, row) -------------------
         for (int task = warp; task < K * R; task += NWARP) {
@@ -480,16 +581,25 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             sstore8(rh, lane, h);
             sstore8(rp, lane, p);
         }
-        cp_async_wait_all();
+        if (use_tma) {
+            tma_wait(1, tph_y);
+            tc::fence_proxy_async();
+        } else {
+            cp_async_wait_all();
+        }
         __syncthreads();
 
         // next iteration's x-pass coefficients and level-0 rows land while the
         // y-pass runs
-        if (it + 1 < nit) {
-            copy_xstash(it + 1);
-            if (active(0, it + 1)) copy_state0(it + 1, cur ^ 1);
+        if (use_tma) {
+            if (it + 1 < nit) tma_group_x(it + 1, active(0, it + 1), cur ^ 1);
+        } else {
+            if (it + 1 < nit) {
+                copy_xstash(it + 1);
+                if (active(0, it + 1)) copy_state0(it + 1, cur ^ 1);
+            }
+            cp_async_commit();
         }
-        cp_async_commit();
 
         // ---- phase 2: y-pass, one thread per (level, column) --------------
         // The NY column pipelines of a thread advance row by row together so
@@ -571,16 +681,68 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         else rows(std::integral_constant<bool, false>());
         itcur = it + 1;
         r0w = wrap_down(r0w + R, Ny);
-        cp_async_wait_all();
+        if (use_tma) {
+            if (it + 1 < nit) tma_wait(0, tph_x);
+            tc::fence_proxy_async();
+        } else {
+            cp_async_wait_all();
+        }
         __syncthreads();
     }
 }
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
-__global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB) sweep_kernel(const SweepParams prm) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (prm.a.fam0 + int(blockIdx.z) == 0) sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw);
-    else sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw);
+__global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB)
+    sweep_kernel(const __grid_constant__ SweepParams prm) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const CUtensorMap *ts = prm.tma ? &prm.tm_state : nullptr;
+    const CUtensorMap *tcf = prm.tma ? &prm.tm_coef : nullptr;
+    if (prm.a.fam0 + int(blockIdx.z) == 0)
+        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf);
+    else
+        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return EncodeTiledFn(nullptr);
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor maps of one FP32 pass (see SweepParams); false when TMA cannot be used
+// (Nx not a multiple of 8, no encoder), in which case the kernel copies with cp.async.
+inline bool make_sweep_maps(const SweepArgs &a, SweepParams &prm) {
+    const EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn || a.Nx % 8 != 0) return false;
+    const cuuint64_t Nx = cuuint64_t(a.Nx), Ny = cuuint64_t(a.Ny);
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    const cuuint64_t sdim[4] = {8, Nx / 8, Ny, 6};
+    const cuuint64_t sstr[3] = {32, Nx * 4, Nx * Ny * 4};
+    const cuuint32_t sbox[4] = {8, 32, 1, 1};
+    if (fn(&prm.tm_state, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.q_in), sdim, sstr, sbox, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t cdim[4] = {16, Nx / 8, Ny, cuuint64_t(NPAIR)};
+    const cuuint64_t cstr[3] = {64, Nx * 8, Nx * Ny * 8};
+    const cuuint32_t cbox[4] = {16, 32, 1, 1};
+    return fn(&prm.tm_coef, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, cbox, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
@@ -612,7 +774,9 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
         configured_dev = dev;
     }
     SweepParams prm;
+    memset(&prm, 0, sizeof(prm));
     prm.a = a;
+    if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, prm)) ? 1 : 0;
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
     dim3 grid(nsx, ncy, nfam);
