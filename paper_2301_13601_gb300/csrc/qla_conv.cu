@@ -74,7 +74,8 @@ struct ConvLayout {
     static constexpr int B_OFF = ((A_BYTES + 1023) / 1024) * 1024;
     static constexpr int SMEM = B_OFF + B_BYTES;
     static constexpr int ACC_COLS = NOUT < 32 ? 32 : NOUT;  // TMEM columns of one accumulator
-    static constexpr int TMEM_COLS = 2 * ACC_COLS;          // two accumulators
+    static constexpr int NACC = 4;                          // accumulators in TMEM
+    static constexpr int TMEM_COLS = NACC * ACC_COLS;
 };
 
 constexpr int CONV_EPI_WARPS = 8;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
     constexpr int NS = L::NS;
     constexpr int HP = L::HALO_PX;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full_bar[NS], empty_bar[NS], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint64_t full_bar[NS], empty_bar[NS], accf_bar[L::NACC], acce_bar[L::NACC], done_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ float bias_s[64];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -155,11 +156,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             tc::mbar_init(&full_bar[s], 32);
-            tc::mbar_init(&empty_bar[s], 1 + CONV_EPI_WARPS);
+            tc::mbar_init(&empty_bar[s], 1 + CONV_EPI_WARPS / 2);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < L::NACC; ++b) {
             tc::mbar_init(&accf_bar[b], 1);
-            tc::mbar_init(&acce_bar[b], CONV_EPI_WARPS);
+            tc::mbar_init(&acce_bar[b], CONV_EPI_WARPS / 2);
         }
         tc::mbar_init(&done_bar, 1);
         tc::fence_mbar_init();
@@ -219,8 +220,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
                     const long long r = g + i + j;
                     if (!tc::mbar_wait(&full_bar[r % NS], uint32_t((r / NS) & 1), CONV_WAIT_TRIES)) ok = false;
                 }
-                const int b = int(o & 1);
-                if (o >= 2 && !tc::mbar_wait(&acce_bar[b], uint32_t(((o >> 1) + 1) & 1), CONV_WAIT_TRIES)) ok = false;
+                const int b = int(o & 3);
+                if (o >= 4 && !tc::mbar_wait(&acce_bar[b], uint32_t(((o >> 2) + 1) & 1), CONV_WAIT_TRIES)) ok = false;
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (lane == 0) {
@@ -261,26 +262,35 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
         if (!ok && lane == 0) atomicExch(a.error, 1);
     } else {
         // ---------------- epilogue ----------------
-        const int q = warp & 3, half = warp >> 2;
-        const bool epi_on = (NOUT >= 64) || half == 0;
+        // Two groups of four warps (grp = warp / 4) take alternate output rows
+        // (o mod 2), so the epilogues of two rows overlap; each warp covers its
+        // TMEM lane quarter and all NOUT columns. Ring rows are released by the
+        // group of the output row they are the centre of (edge rows: the group
+        // of the neighbouring output row), so a slot is always released by the
+        // same group and its arrivals come in order.
+        const int q = warp & 3, grp = warp >> 2;
         const int m = 32 * q + lane;
-        const int cb0 = (NOUT >= 64 ? 32 * half : 0);
         constexpr int NC = NOUT < 32 ? NOUT : 32;
+        constexpr int NCB = NOUT >= 64 ? 2 : 1;
         const bool res_smem = a.epi == EPI_GELU && a.aux0 != nullptr && a.aux0 == a.x && CIN == NOUT;
         long long o = 0, g = 0;
         bool ok = true;
         for (long long u0 = u_begin; u0 < u_end && ok;) {
             const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
+            const long long o_seg = o;
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty_bar[g % NS]);  // first halo row: no epilogue reads it
+            if (lane == 0 && int((o_seg - 1) & 1) == grp) mbar_arrive(&empty_bar[g % NS]);  // first halo row
             for (int i = 0; i < sg.len; ++i, ++o) {
-                const int b = int(o & 1);
-                if (!tc::mbar_wait(&accf_bar[b], uint32_t((o >> 1) & 1), CONV_WAIT_TRIES)) {
+                if (int(o & 1) != grp) continue;
+                const int b = int(o & 3);
+                if (!tc::mbar_wait(&accf_bar[b], uint32_t((o >> 2) & 1), CONV_WAIT_TRIES)) {
                     ok = false;
                     break;
                 }
                 tc::fence_after_sync();
-                if (epi_on) {
+#pragma unroll 1
+                for (int cbi = 0; cbi < NCB; ++cbi) {
+                    const int cb0 = 32 * cbi;
                     const int y = sg.y_s + i;
                     const size_t p = ((size_t)sg.img * H + y) * W + sg.x0 + m;
                     float v[32];
@@ -374,7 +384,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
             }
             if (!ok) break;
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty_bar[(g + sg.len + 1) % NS]);  // last halo row
+            if (lane == 0 && int((o_seg + sg.len) & 1) == grp)
+                mbar_arrive(&empty_bar[(g + sg.len + 1) % NS]);  // last halo row
             g += sg.len + 2;
             u0 += sg.len;
         }
