@@ -79,6 +79,22 @@ def test_fp32_matches_oracle(shape, K, sequence, potential):
     assert rel_l2(got, ref) < 3e-6
 
 
+@pytest.mark.parametrize("K", [2, 4])
+@pytest.mark.parametrize("sequence", ["interleaved", "plain"])
+@pytest.mark.parametrize("potential", ["paper", "unitary"])
+def test_fp32_tma_strips_match_oracle(K, sequence, potential):
+    """Nx a multiple of 8 and several strips: the inner strips load their rows
+    with TMA, the two that wrap around x with cp.async; both must agree with
+    the oracle (rows in tiles of 40 with a ragged last tile)."""
+    Nx, Ny, chunk = 1024, 96, 40
+    n, q0 = problem(Nx, Ny, seed=5)
+    delta, steps = 0.2, 3 * K + 1
+    got = gpu_run(n, q0, delta, steps, precision="fp32", steps_per_pass=K, chunk_rows=chunk,
+                  sequence=sequence, potential=potential)
+    ref = oracle_run(n, q0, delta, steps, sequence, potential)
+    assert rel_l2(got, ref) < 3e-6
+
+
 def test_pulse_init_matches_oracle():
     for pol, name in ((0, "Ez"), (1, "Ey")):
         Nx, Ny = 300, 20
