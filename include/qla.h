@@ -188,7 +188,10 @@ qla_status qla_get_fields_f32(qla_ctx *ctx, float *q);
  * double, per the precision). Valid until the next qla_step. */
 void *qla_state_device_ptr(qla_ctx *ctx);
 
-/* Block the host until all queued work of the context has finished. */
+/* Block the host until all queued work of the context has finished.
+ * QLA_ETIMEOUT (sticky) if a sweep's bounded wait for its TMA row copies ran
+ * out since creation; the state is then invalid. qla_diagnostics reports the
+ * same condition. */
 qla_status qla_synchronize(qla_ctx *ctx);
 
 /* Steps taken since the last state reset; -1 for a NULL context. */

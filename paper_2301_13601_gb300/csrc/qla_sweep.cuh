@@ -25,11 +25,13 @@
 //    recomputed. The y-pass of level j writes level j+1's row buffer (double
 //    buffered) or, for the last level, global memory.
 //  * No compute phase touches global memory for its inputs: the y-pass
-//    coefficients of an iteration are copied into shared memory with cp.async
-//    while the x-pass of that iteration runs, and the x-pass coefficients and
-//    next level-0 rows while the y-pass of the previous iteration runs. (A
-//    bulk L2 prefetch two iterations ahead was measured to cost 18% on top of
-//    this staging and is not used.)
+//    coefficients of an iteration are copied into shared memory while the
+//    x-pass of that iteration runs, and the x-pass coefficients and next
+//    level-0 rows while the y-pass of the previous iteration runs. The copies
+//    are TMA tile loads (one row per load, mbarrier completion) where the strip
+//    does not wrap around x, per-lane cp.async elsewhere. (A bulk L2 prefetch
+//    two iterations ahead was measured to cost 18% on top of this staging and
+//    is not used.)
 //  * Rotations use the (cos-1, sin) form h' = h + (m h + s p): one rounding at
 //    the scale of h per output, with coefficients whose FP32 norm error is
 //    minimised at creation. Coefficients are stored as (m, s) pairs.
