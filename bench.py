@@ -33,7 +33,9 @@ sys.path.insert(0, ROOT)
 # DRAM bytes per sweep launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on the default workload; valid only for the kernel source it was measured on
 # (profiles/sweep_kernel_cylinders8192_launches.md).
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "35a058aae99d0f8b", "workload": "cylinders8192_fp32",
+# DRAM bytes per sweep launch from one ncu capture (profiles/sweep_kernel_cylinders8192_launches.md), valid
+# while the sweep's code (comment lines excluded), the workload, steps per pass and rows per tile match.
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "94dfb3fc4ff6ba65", "workload": "cylinders8192_fp32",
                     "steps_per_pass": 4, "chunk_rows": 1024, "bytes_per_launch": 5.701e9 + 1.593e9}
 
 METRIC = "site-updates/s per QLA step"
@@ -108,6 +110,15 @@ class ClockSampler:
         pw = [num(r[2]) for r in self.rows if num(r[2]) is not None]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def sweep_code_hash() -> str:
+    """sha256 prefix of the sweep kernel source with its comment lines removed."""
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", "qla_sweep.cuh")) as f:
+        code = "\n".join(l for l in f.read().splitlines() if not l.lstrip().startswith("//"))
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def job_throughput(units: float, elapsed_ms: float, world: int, device=None):
@@ -276,9 +287,7 @@ def run_ours(args):
         return
     peak, peak_kind = measured_peaks()
     k = sim.steps_per_pass
-    import hashlib
-    with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", "qla_sweep.cuh"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    sha = sweep_code_hash()
     traffic = None
     if (sha == MEASURED_TRAFFIC["sweep_sha256_prefix"] and w.name == MEASURED_TRAFFIC["workload"]
             and k == MEASURED_TRAFFIC["steps_per_pass"] and sim.chunk_rows == MEASURED_TRAFFIC["chunk_rows"]):
