@@ -97,15 +97,25 @@ int sm_count(int dev) {
     return n;
 }
 
-// Rows per tile: choose the number of row chunks that minimises
-// (waves of CTAs) x (rows swept per CTA, warm-up included).
+// Default steps per pass. FP32: K = 2 (two CTAs per SM, 112 KB of shared
+// memory each) on lattices of at least 2^25 sites, else K = 4 (one 224 KB CTA
+// per SM). Measured on GB300, site-updates/s: 8192^2 K = 2 50.9 G vs K = 4
+// 45.2 G; 4096^2 41.1 G vs 42.5 G; 2048^2 30.4 G vs 34.2 G; 1024^2 19.3 G vs
+// 24.8 G: the second resident CTA pays only when there are enough tiles.
+int default_steps_per_pass(int precision, int Nx, int Ny) {
+    if (precision == QLA_FP64) return 2;
+    return (long long)Nx * Ny >= (1LL << 25) ? 2 : 4;
+}
+
 // Rows per tile: the fewest waves x (rows + warm-up rows) among tiles of at
-// most kMaxAutoChunk rows. The cap is measured, not modelled: on the 8192^2
-// workload (K = 4) tiles of 512-1280 rows run 39-40 G site-updates/s against
-// 36 G for the single-wave 4096-row split the wave model alone prefers.
-constexpr int kMaxAutoChunk = 1024;
+// most max_auto_chunk(K) rows. The caps are measured, not modelled: on the
+// 8192^2 workload tiles of 512-1280 rows (K = 4) and 256-640 rows (K = 2, best
+// 384) beat the few-wave splits the wave model alone prefers (K = 4: 39-40 G
+// vs 36 G for 4096 rows; K = 2: 50.9 G at 384 rows vs 46 G at 768).
+int max_auto_chunk(int K) { return K == 2 ? 384 : 1024; }
 
 int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
+    const int kMaxAutoChunk = max_auto_chunk(K);
     const int W = qla::sweep_strip_width();
     const int wv = W - 8 * K;
     const int nsx = (Nx + wv - 1) / wv;
@@ -288,7 +298,7 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
         cudaMemsetAsync(c->state[1], 0, bs.state_bytes, c->stream) != cudaSuccess)
         return bail(QLA_ECUDA);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(QLA_ECUDA);
-    c->K = o.steps_per_pass > 0 ? o.steps_per_pass : (o.precision == QLA_FP64 ? 2 : 4);
+    c->K = o.steps_per_pass > 0 ? o.steps_per_pass : default_steps_per_pass(o.precision, Nx, Ny);
     c->chunk = o.chunk_rows > 0 ? std::min(o.chunk_rows, Ny)
                                 : auto_chunk(Nx, Ny, c->K, o.precision == QLA_FP64 ? 1 : 0, sm_count(c->dev));
     c->has_state = true;  // zero state

@@ -298,8 +298,8 @@ struct SweepLayout {
     static constexpr size_t STATE = size_t(K) * 2 * 3 * R * W_IN * sizeof(T);
     static constexpr size_t YST = size_t(K) * NYS * R * W_IN * sizeof(T2);
     static constexpr size_t XST = size_t(K) * NXS * R * W_IN * sizeof(T2);
-    static constexpr size_t BAR_OFF = STATE + YST + XST;  // two mbarriers of the TMA copy groups
-    static constexpr size_t SMEM = BAR_OFF + 64;
+    static constexpr size_t BAR_OFF = STATE + YST + XST;  // mbarriers of the TMA copies, two per row index
+    static constexpr size_t SMEM = BAR_OFF + 16 * R;
 };
 
 template <typename T, int K, int R, int NY>
@@ -420,57 +420,60 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     };
 
     // TMA path (FP32, a strip that does not wrap around x, 8-column aligned):
-    // warp 0 issues each copy group, one row per TMA load; lane 0 first posts
-    // the group's byte count on its mbarrier (group X: x-pass coefficients and
-    // level-0 state rows; group Y: y-pass coefficients), and every thread waits
-    // on the mbarrier where the cp.async path waits for its groups.
+    // warp 0 issues each copy group, one row per TMA load, lanes 0..R-1 first
+    // posting the byte count of each row index on its mbarrier (group X: x-pass
+    // coefficients and level-0 state rows; group Y: y-pass coefficients). The
+    // consumers wait inside the next phase for their own row index only, so the
+    // copies of later rows overlap the work on earlier ones.
     uint64_t *const tbar = reinterpret_cast<uint64_t *>(smem_raw + L::BAR_OFF);
     bool use_tma = false;
     if constexpr (std::is_same<T, float>::value)
         use_tma = tm_state != nullptr && tm_coef != nullptr && nowrap && (xb & 7) == 0 &&
                   (tc::smem_addr(smem_raw) & 1023u) == 0;
+    // one mbarrier per row index ir and group: X[ir] = tbar[ir], Y[ir] = tbar[R + ir]; a
+    // consumer waits only for its own rows (x-pass warp of row ir, y-pass row step ir)
     uint32_t tph_x = 0, tph_y = 0;
     constexpr uint32_t SROW = W_IN * sizeof(T), CROW = W_IN * sizeof(T2);
     auto tma_group_x = [&](int it, bool with_state, int half) {
         if (warp != 0) return;
-        int nrows = 0;
+        int nlev = 0;
         for (int j = 0; j < K; ++j)
-            if (active(j, it)) nrows += NXS * R;
-        const uint32_t bytes = uint32_t(nrows) * CROW + (with_state ? 3u * R * SROW : 0u);
+            if (active(j, it)) ++nlev;
+        const uint32_t bytes = uint32_t(nlev * NXS) * CROW + (with_state ? 3u * SROW : 0u);  // per row index
         tc::fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(&tbar[0], bytes);
+        if (lane < R) mbar_arrive_expect_tx(&tbar[lane], bytes);
         __syncwarp();
         for (int task = lane; task < K * NXS * R; task += 32) {
-            const int j = task / (NXS * R), rem = task % (NXS * R);
-            const int slot = rem / R, ir = rem % R;
+            const int ir = task % R, rem = task / R;  // row index fastest: early rows are issued first
+            const int j = rem / NXS, slot = rem % NXS;
             if (!active(j, it)) continue;
-            tma_row(xstrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir), slot == 0 ? Fm::CX : Fm::VX, &tbar[0]);
+            tma_row(xstrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir), slot == 0 ? Fm::CX : Fm::VX,
+                    &tbar[ir]);
         }
         if (with_state) {
             for (int task = lane; task < 3 * R; task += 32) {
                 const int comp = task / R, ir = task % R;
                 tma_row(bufrow(0, half, comp, ir), tm_state, xb >> 3, growof(0, it, ir),
-                        comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[0]);
+                        comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[ir]);
             }
         }
     };
     auto tma_group_y = [&](int it) {
         if (warp != 0) return;
         tc::fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(&tbar[1], uint32_t(K * NYS * R) * CROW);
+        if (lane < R) mbar_arrive_expect_tx(&tbar[R + lane], uint32_t(K * NYS) * CROW);
         __syncwarp();
         for (int task = lane; task < K * NYS * R; task += 32) {
-            const int j = task / (NYS * R), rem = task % (NYS * R);
-            const int slot = rem / R, ir = rem % R;
+            const int ir = task % R, rem = task / R;
+            const int j = rem / NYS, slot = rem % NYS;
             tma_row(ystrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir),
-                    slot == 0 ? Fm::CY : (slot == 1 ? Fm::VY : Fm::VX), &tbar[1]);
+                    slot == 0 ? Fm::CY : (slot == 1 ? Fm::VY : Fm::VX), &tbar[R + ir]);
         }
     };
     // bounded wait for a copy group; a timeout sets the error flag (the
     // results of the launch are then invalid) instead of hanging
-    auto tma_wait = [&](int b, uint32_t &ph) {
+    auto tma_wait = [&](int b, uint32_t ph) {
         if (!tc::mbar_wait(&tbar[b], ph, 1u << 24) && A.error) atomicExch(A.error, 1);
-        ph ^= 1u;
     };
 
     for (int i = tid; i < int(L::STATE / sizeof(T)); i += NT) buf[i] = T(0);
@@ -504,14 +507,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     // before the barrier that precedes an issue
     if (use_tma) tc::fence_proxy_async();
     if (use_tma && tid == 0) {
-        tc::mbar_init(&tbar[0], 1);
-        tc::mbar_init(&tbar[1], 1);
+        for (int b = 0; b < 2 * R; ++b) tc::mbar_init(&tbar[b], 1);
         tc::fence_mbar_init();
     }
     __syncthreads();  // zeroed buffers before the async copies land
     if (use_tma) {
-        tma_group_x(0, true, 0);
-        tma_wait(0, tph_x);
+        tma_group_x(0, true, 0);  // consumed row by row in the first x-pass
     } else {
         copy_state0(0, 0);
         copy_xstash(0);
@@ -537,6 +538,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         for (int task = warp; task < K * R; task += NWARP) {
             const int j = task / R, ir = task % R;
             if (!active(j, it)) continue;
+            if (use_tma) {
+                tma_wait(ir, tph_x);
+                tc::fence_after_sync();
+            }
             T *rh = bufrow(j, cur, 0, ir);
             T *rp = bufrow(j, cur, 1, ir);
             T m[LANE_COLS], s[LANE_COLS], h[LANE_COLS], p[LANE_COLS];
@@ -584,7 +589,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             sstore8(rp, lane, p);
         }
         if (use_tma) {
-            tma_wait(1, tph_y);
+            tph_x ^= 1u;
             tc::fence_proxy_async();
         } else {
             cp_async_wait_all();
@@ -616,6 +621,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             constexpr bool FINAL = decltype(final_tag)::value;
 #pragma unroll
             for (int ir = 0; ir < R; ++ir) {
+                if (use_tma) {  // this row's y-pass coefficients (all levels) have landed
+                    tma_wait(R + ir, tph_y);
+                    tc::fence_after_sync();
+                }
 #pragma unroll
                 for (int u = 0; u < NY; ++u) {
                     YPipe<T> &Y = yp[u];
@@ -684,7 +693,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         itcur = it + 1;
         r0w = wrap_down(r0w + R, Ny);
         if (use_tma) {
-            if (it + 1 < nit) tma_wait(0, tph_x);
+            tph_y ^= 1u;
             tc::fence_proxy_async();
         } else {
             cp_async_wait_all();
