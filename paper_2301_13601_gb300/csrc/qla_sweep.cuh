@@ -52,13 +52,17 @@ constexpr int W_IN = 32 * LANE_COLS;
 
 struct SweepParams {
     SweepArgs a;
-    // Tensor maps for the TMA row loads (FP32, used when tma != 0): the input
+    // Tensor maps for the TMA loads (FP32, used when tma != 0): the input
     // state viewed as [6][Ny][Nx/8][8] floats with the 32-byte swizzle and the
     // coefficient pairs as [7][Ny][Nx/8][16] floats with the 64-byte swizzle.
-    // One box (8 x 32, resp. 16 x 32) is one 256-column strip row, landing in
-    // exactly the XOR-swizzled layout of the shared row buffers (swz below).
+    // One box row (8 x 32, resp. 16 x 32) is one 256-column strip row, landing
+    // in exactly the XOR-swizzled layout of the shared row buffers (swz below).
+    // The *_r maps load R consecutive rows (a whole row block) per box; the
+    // one-row maps serve blocks that wrap around y.
     CUtensorMap tm_state;
     CUtensorMap tm_coef;
+    CUtensorMap tm_state_r;
+    CUtensorMap tm_coef_r;
     int tma;
 };
 
@@ -252,8 +256,8 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// One strip row by TMA: the box at (0, c1, c2, c3) of `map` into `dst`,
-// completing `bytes` on the mbarrier.
+// One box by TMA: the box at (0, c1, c2, c3) of `map` into `dst`, completing
+// its bytes on the mbarrier.
 __device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *map, int c1, int c2, int c3, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
@@ -298,8 +302,8 @@ struct SweepLayout {
     static constexpr size_t STATE = size_t(K) * 2 * 3 * R * W_IN * sizeof(T);
     static constexpr size_t YST = size_t(K) * NYS * R * W_IN * sizeof(T2);
     static constexpr size_t XST = size_t(K) * NXS * R * W_IN * sizeof(T2);
-    static constexpr size_t BAR_OFF = STATE + YST + XST;  // mbarriers of the TMA copies, two per row index
-    static constexpr size_t SMEM = BAR_OFF + 16 * R;
+    static constexpr size_t BAR_OFF = STATE + YST + XST;  // mbarriers of the two TMA copy groups
+    static constexpr size_t SMEM = BAR_OFF + 16;
 };
 
 template <typename T, int K, int R, int NY>
@@ -333,7 +337,9 @@ struct YPipe {
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
 __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int chunk_idx, unsigned char *smem_raw,
                                            const CUtensorMap *tm_state = nullptr,
-                                           const CUtensorMap *tm_coef = nullptr) {
+                                           const CUtensorMap *tm_coef = nullptr,
+                                           const CUtensorMap *tm_state_r = nullptr,
+                                           const CUtensorMap *tm_coef_r = nullptr) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     using T2 = typename Ar<T>::T2;
@@ -419,55 +425,59 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         }
     };
 
-    // TMA path (FP32, a strip that does not wrap around x, 8-column aligned):
-    // warp 0 issues each copy group, one row per TMA load, lanes 0..R-1 first
-    // posting the byte count of each row index on its mbarrier (group X: x-pass
-    // coefficients and level-0 state rows; group Y: y-pass coefficients). The
-    // consumers wait inside the next phase for their own row index only, so the
-    // copies of later rows overlap the work on earlier ones.
+    // TMA path (FP32, a strip that does not wrap around x, 8-column aligned).
+    // Group X (x-pass coefficients of every active level and the level-0 state
+    // rows) and group Y (y-pass coefficients) each complete on one mbarrier.
+    // Each box carries the R rows of one (level, plane) block, so a group is
+    // 3 + K * NXS (resp. K * NYS) loads, issued by lane 0 of as many warps:
+    // measured on GB300, per-row loads issued by one warp cost a quarter of the
+    // kernel's time, the issue itself being the bottleneck.
     uint64_t *const tbar = reinterpret_cast<uint64_t *>(smem_raw + L::BAR_OFF);
     bool use_tma = false;
     if constexpr (std::is_same<T, float>::value)
-        use_tma = tm_state != nullptr && tm_coef != nullptr && nowrap && (xb & 7) == 0 &&
-                  (tc::smem_addr(smem_raw) & 1023u) == 0;
-    // one mbarrier per row index ir and group: X[ir] = tbar[ir], Y[ir] = tbar[R + ir]; a
-    // consumer waits only for its own rows (x-pass warp of row ir, y-pass row step ir)
+        use_tma = tm_state != nullptr && tm_coef != nullptr && tm_state_r != nullptr && tm_coef_r != nullptr &&
+                  nowrap && (xb & 7) == 0 && (tc::smem_addr(smem_raw) & 1023u) == 0;
     uint32_t tph_x = 0, tph_y = 0;
     constexpr uint32_t SROW = W_IN * sizeof(T), CROW = W_IN * sizeof(T2);
+    // the R rows of a block from global row r0 on: one box, or R one-row boxes
+    // where the block wraps around y
+    auto tma_block = [&](void *dst, uint32_t row_bytes, const CUtensorMap *one, const CUtensorMap *blk, int j,
+                         int it, int plane, uint64_t *bar) {
+        const int r0 = growof(j, it, 0);
+        if (r0 + R <= Ny) {
+            tma_row(dst, blk, xb >> 3, r0, plane, bar);
+        } else {
+            for (int ir = 0; ir < R; ++ir)
+                tma_row(static_cast<unsigned char *>(dst) + ir * row_bytes, one, xb >> 3, growof(j, it, ir), plane,
+                        bar);
+        }
+    };
     auto tma_group_x = [&](int it, bool with_state, int half) {
-        if (warp != 0) return;
         int nlev = 0;
         for (int j = 0; j < K; ++j)
             if (active(j, it)) ++nlev;
-        const uint32_t bytes = uint32_t(nlev * NXS) * CROW + (with_state ? 3u * SROW : 0u);  // per row index
-        tc::fence_proxy_async();
-        if (lane < R) mbar_arrive_expect_tx(&tbar[lane], bytes);
-        __syncwarp();
-        for (int task = lane; task < K * NXS * R; task += 32) {
-            const int ir = task % R, rem = task / R;  // row index fastest: early rows are issued first
-            const int j = rem / NXS, slot = rem % NXS;
-            if (!active(j, it)) continue;
-            tma_row(xstrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir), slot == 0 ? Fm::CX : Fm::VX,
-                    &tbar[ir]);
-        }
-        if (with_state) {
-            for (int task = lane; task < 3 * R; task += 32) {
-                const int comp = task / R, ir = task % R;
-                tma_row(bufrow(0, half, comp, ir), tm_state, xb >> 3, growof(0, it, ir),
-                        comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[ir]);
+        const uint32_t row_bytes = uint32_t(nlev * NXS) * CROW + (with_state ? 3u * SROW : 0u);
+        if (tid == 0) mbar_arrive_expect_tx(&tbar[0], uint32_t(R) * row_bytes);
+        const int ntask = K * NXS + (with_state ? 3 : 0);
+        for (int t = warp + NWARP * lane; t < ntask; t += 32 * NWARP) {
+            if (t < K * NXS) {
+                const int j = t / NXS, slot = t % NXS;
+                if (active(j, it))
+                    tma_block(xstrow(j, slot, 0), CROW, tm_coef, tm_coef_r, j, it, slot == 0 ? Fm::CX : Fm::VX,
+                              &tbar[0]);
+            } else {
+                const int comp = t - K * NXS;
+                tma_block(bufrow(0, half, comp, 0), SROW, tm_state, tm_state_r, 0, it,
+                          comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[0]);
             }
         }
     };
     auto tma_group_y = [&](int it) {
-        if (warp != 0) return;
-        tc::fence_proxy_async();
-        if (lane < R) mbar_arrive_expect_tx(&tbar[R + lane], uint32_t(K * NYS) * CROW);
-        __syncwarp();
-        for (int task = lane; task < K * NYS * R; task += 32) {
-            const int ir = task % R, rem = task / R;
-            const int j = rem / NYS, slot = rem % NYS;
-            tma_row(ystrow(j, slot, ir), tm_coef, xb >> 3, growof(j, it, ir),
-                    slot == 0 ? Fm::CY : (slot == 1 ? Fm::VY : Fm::VX), &tbar[R + ir]);
+        if (tid == 0) mbar_arrive_expect_tx(&tbar[1], uint32_t(R * K * NYS) * CROW);
+        for (int t = warp + NWARP * lane; t < K * NYS; t += 32 * NWARP) {
+            const int j = t / NYS, slot = t % NYS;
+            tma_block(ystrow(j, slot, 0), CROW, tm_coef, tm_coef_r, j, it,
+                      slot == 0 ? Fm::CY : (slot == 1 ? Fm::VY : Fm::VX), &tbar[1]);
         }
     };
     // bounded wait for a copy group; a timeout sets the error flag (the
@@ -502,17 +512,19 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     T *const qo_px = qout + size_t(Fm::PX) * P + gx;
     T *const qo_py = qout + size_t(Fm::PY) * P + gx;
 
-    // generic writes and reads of shared memory are ordered before the TMA
-    // (async proxy) writes that later reuse the same rows: every thread fences
-    // before the barrier that precedes an issue
+    // Generic writes of shared memory that a TMA load later overwrites (the
+    // zeroing here, the x-pass's in-place level-0 rows) are fenced to the async
+    // proxy by their writers before the barrier that precedes the issue. Rows
+    // that threads only read are reused after a barrier alone.
     if (use_tma) tc::fence_proxy_async();
     if (use_tma && tid == 0) {
-        for (int b = 0; b < 2 * R; ++b) tc::mbar_init(&tbar[b], 1);
+        tc::mbar_init(&tbar[0], 1);
+        tc::mbar_init(&tbar[1], 1);
         tc::fence_mbar_init();
     }
     __syncthreads();  // zeroed buffers before the async copies land
     if (use_tma) {
-        tma_group_x(0, true, 0);  // consumed row by row in the first x-pass
+        tma_group_x(0, true, 0);  // waited for in the first x-pass
     } else {
         copy_state0(0, 0);
         copy_xstash(0);
@@ -539,7 +551,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             const int j = task / R, ir = task % R;
             if (!active(j, it)) continue;
             if (use_tma) {
-                tma_wait(ir, tph_x);
+                tma_wait(0, tph_x);
                 tc::fence_after_sync();
             }
             T *rh = bufrow(j, cur, 0, ir);
@@ -587,10 +599,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             }
             sstore8(rh, lane, h);
             sstore8(rp, lane, p);
+            if (use_tma && j == 0) tc::fence_proxy_async();  // level-0 rows are TMA targets again later
         }
         if (use_tma) {
             tph_x ^= 1u;
-            tc::fence_proxy_async();
         } else {
             cp_async_wait_all();
         }
@@ -617,14 +629,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         // keeps the loop-carried pipeline registers free of merge copies.
         const int hin = cur * HALF, hout = (cur ^ 1) * HALF;
         const int rout0 = arow(yj[NY - 1], it) - 4;  // first output row of the last slot
+        if (use_tma) {  // the y-pass coefficients of all levels have landed
+            tma_wait(1, tph_y);
+            tc::fence_after_sync();
+        }
         auto rows = [&](auto final_tag) {
             constexpr bool FINAL = decltype(final_tag)::value;
 #pragma unroll
             for (int ir = 0; ir < R; ++ir) {
-                if (use_tma) {  // this row's y-pass coefficients (all levels) have landed
-                    tma_wait(R + ir, tph_y);
-                    tc::fence_after_sync();
-                }
 #pragma unroll
                 for (int u = 0; u < NY; ++u) {
                     YPipe<T> &Y = yp[u];
@@ -694,7 +706,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         r0w = wrap_down(r0w + R, Ny);
         if (use_tma) {
             tph_y ^= 1u;
-            tc::fence_proxy_async();
         } else {
             cp_async_wait_all();
         }
@@ -709,9 +720,11 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
     const CUtensorMap *ts = prm.tma ? &prm.tm_state : nullptr;
     const CUtensorMap *tcf = prm.tma ? &prm.tm_coef : nullptr;
     if (prm.a.fam0 + int(blockIdx.z) == 0)
-        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf);
+        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf, &prm.tm_state_r,
+                                                &prm.tm_coef_r);
     else
-        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf);
+        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf, &prm.tm_state_r,
+                                                &prm.tm_coef_r);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -736,7 +749,7 @@ inline EncodeTiledFn encode_tiled_fn() {
 
 // Tensor maps of one FP32 pass (see SweepParams); false when TMA cannot be used
 // (Nx not a multiple of 8, no encoder), in which case the kernel copies with cp.async.
-inline bool make_sweep_maps(const SweepArgs &a, SweepParams &prm) {
+inline bool make_sweep_maps(const SweepArgs &a, int R, SweepParams &prm) {
     const EncodeTiledFn fn = encode_tiled_fn();
     if (!fn || a.Nx % 8 != 0) return false;
     const cuuint64_t Nx = cuuint64_t(a.Nx), Ny = cuuint64_t(a.Ny);
@@ -748,9 +761,19 @@ inline bool make_sweep_maps(const SweepArgs &a, SweepParams &prm) {
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
+    const cuuint32_t sboxr[4] = {8, 32, cuuint32_t(R), 1};
+    if (fn(&prm.tm_state_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.q_in), sdim, sstr, sboxr, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
     const cuuint64_t cdim[4] = {16, Nx / 8, Ny, cuuint64_t(NPAIR)};
     const cuuint64_t cstr[3] = {64, Nx * 8, Nx * Ny * 8};
     const cuuint32_t cbox[4] = {16, 32, 1, 1};
+    const cuuint32_t cboxr[4] = {16, 32, cuuint32_t(R), 1};
+    if (fn(&prm.tm_coef_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, cboxr, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
     return fn(&prm.tm_coef, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, cbox, one,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -787,7 +810,7 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     SweepParams prm;
     memset(&prm, 0, sizeof(prm));
     prm.a = a;
-    if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, prm)) ? 1 : 0;
+    if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, R, prm)) ? 1 : 0;
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
     dim3 grid(nsx, ncy, nfam);
