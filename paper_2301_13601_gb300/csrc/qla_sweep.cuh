@@ -63,7 +63,12 @@ struct SweepParams {
     CUtensorMap tm_coef;
     CUtensorMap tm_state_r;
     CUtensorMap tm_coef_r;
+    // The coefficient pairs as [7][Ny / (R + 4)][R + 4][Nx/8][16] floats: one
+    // box (16 x 32 x R x K) holds the R-row blocks of all K levels of an
+    // iteration, which start R + 4 rows apart (used when merged != 0).
+    CUtensorMap tm_coef_m;
     int tma;
+    int merged;
 };
 
 template <typename T>
@@ -265,6 +270,15 @@ __device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *map, int c
         "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::smem_addr(bar))
         : "memory");
 }
+// The box at (0, c1, c2, c3, c4) of a five-dimensional `map` into `dst`.
+__device__ __forceinline__ void tma_box5(void *dst, const CUtensorMap *map, int c1, int c2, int c3, int c4,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];\n" ::"r"(tc::smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(tc::smem_addr(bar))
+        : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -339,7 +353,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                                            const CUtensorMap *tm_state = nullptr,
                                            const CUtensorMap *tm_coef = nullptr,
                                            const CUtensorMap *tm_state_r = nullptr,
-                                           const CUtensorMap *tm_coef_r = nullptr) {
+                                           const CUtensorMap *tm_coef_r = nullptr,
+                                           const CUtensorMap *tm_coef_m = nullptr) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     using T2 = typename Ar<T>::T2;
@@ -375,8 +390,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     auto bufrow = [&](int j, int half, int comp, int ir) -> T * {
         return buf + ((((j * 2 + half) * 3 + comp) * R + ir) * W_IN);
     };
-    auto ystrow = [&](int j, int slot, int ir) -> T2 * { return yst + (((j * NYS + slot) * R + ir) * W_IN); };
-    auto xstrow = [&](int j, int slot, int ir) -> T2 * { return xst + (((j * NXS + slot) * R + ir) * W_IN); };
+    // coefficient stashes: [slot][level K-1 .. 0][R rows], the order of a
+    // merged TMA box (level K-1's block has the lowest global rows)
+    auto ystrow = [&](int j, int slot, int ir) -> T2 * { return yst + (((slot * K + K - 1 - j) * R + ir) * W_IN); };
+    auto xstrow = [&](int j, int slot, int ir) -> T2 * { return xst + (((slot * K + K - 1 - j) * R + ir) * W_IN); };
     // first (unwrapped) row handled by level j in iteration it
     auto arow = [&](int j, int it) { return F0 + (it - j) * R - 4 * j; };
     auto active = [&](int j, int it) { return it >= j && arow(j, it) <= ye - 1 + 4 * (K - j); };
@@ -452,21 +469,32 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                         bar);
         }
     };
+    // the blocks of one coefficient plane for all K levels: one merged box
+    // where they neither wrap around y nor straddle a group of R + 4 rows,
+    // else one box (or R one-row boxes) per level
+    const bool merge_ok = tm_coef_m != nullptr && K > 1;
+    auto tma_plane = [&](bool ystash, int slot, int it, int plane, uint64_t *bar) {
+        T2 *const top = ystash ? ystrow(K - 1, slot, 0) : xstrow(K - 1, slot, 0);
+        const int r_top = growof(K - 1, it, 0);
+        const int b0 = r_top % (R + 4);
+        if (merge_ok && r_top + (K - 1) * (R + 4) + R <= Ny && b0 <= 4) {
+            tma_box5(top, tm_coef_m, xb >> 3, b0, r_top / (R + 4), plane, bar);
+        } else {
+            for (int j = 0; j < K; ++j)
+                tma_block(ystash ? ystrow(j, slot, 0) : xstrow(j, slot, 0), CROW, tm_coef, tm_coef_r, j, it, plane,
+                          bar);
+        }
+    };
     auto tma_group_x = [&](int it, bool with_state, int half) {
-        int nlev = 0;
-        for (int j = 0; j < K; ++j)
-            if (active(j, it)) ++nlev;
-        const uint32_t row_bytes = uint32_t(nlev * NXS) * CROW + (with_state ? 3u * SROW : 0u);
+        // every level's blocks are loaded (an inactive level's are not read)
+        const uint32_t row_bytes = uint32_t(K * NXS) * CROW + (with_state ? 3u * SROW : 0u);
         if (tid == 0) mbar_arrive_expect_tx(&tbar[0], uint32_t(R) * row_bytes);
-        const int ntask = K * NXS + (with_state ? 3 : 0);
+        const int ntask = NXS + (with_state ? 3 : 0);
         for (int t = warp + NWARP * lane; t < ntask; t += 32 * NWARP) {
-            if (t < K * NXS) {
-                const int j = t / NXS, slot = t % NXS;
-                if (active(j, it))
-                    tma_block(xstrow(j, slot, 0), CROW, tm_coef, tm_coef_r, j, it, slot == 0 ? Fm::CX : Fm::VX,
-                              &tbar[0]);
+            if (t < NXS) {
+                tma_plane(false, t, it, t == 0 ? Fm::CX : Fm::VX, &tbar[0]);
             } else {
-                const int comp = t - K * NXS;
+                const int comp = t - NXS;
                 tma_block(bufrow(0, half, comp, 0), SROW, tm_state, tm_state_r, 0, it,
                           comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[0]);
             }
@@ -474,11 +502,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     };
     auto tma_group_y = [&](int it) {
         if (tid == 0) mbar_arrive_expect_tx(&tbar[1], uint32_t(R * K * NYS) * CROW);
-        for (int t = warp + NWARP * lane; t < K * NYS; t += 32 * NWARP) {
-            const int j = t / NYS, slot = t % NYS;
-            tma_block(ystrow(j, slot, 0), CROW, tm_coef, tm_coef_r, j, it,
-                      slot == 0 ? Fm::CY : (slot == 1 ? Fm::VY : Fm::VX), &tbar[1]);
-        }
+        for (int t = warp + NWARP * lane; t < NYS; t += 32 * NWARP)
+            tma_plane(true, t, it, t == 0 ? Fm::CY : (t == 1 ? Fm::VY : Fm::VX), &tbar[1]);
     };
     // bounded wait for a copy group; a timeout sets the error flag (the
     // results of the launch are then invalid) instead of hanging
@@ -492,7 +517,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     // Only the last slot can hold the last level (tasks are ordered by level).
     constexpr int LVL = 2 * 3 * R * W_IN;   // elements of one level's state buffers
     constexpr int HALF = 3 * R * W_IN;      // one half (3 components x R rows)
-    constexpr int YLVL = NYS * R * W_IN;    // one level's y-stash pairs
+    constexpr int YSLOT = K * R * W_IN;     // one y-stash slot (all levels)
     int yj[NY];
     const T *st_base[NY];
     const T2 *ys_base[NY];
@@ -502,7 +527,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         yj[u] = task / W_IN;
         const int c = task % W_IN;
         st_base[u] = buf + yj[u] * LVL + swz<T>(c);
-        ys_base[u] = yst + yj[u] * YLVL + swz<T2>(c);
+        ys_base[u] = yst + (K - 1 - yj[u]) * R * W_IN + swz<T2>(c);
     }
     const int c_last = (tid + (NY - 1) * NT) % W_IN;
     const bool last_is_final = yj[NY - 1] == K - 1;  // uniform per warp
@@ -643,8 +668,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     constexpr int SG = Fm::SGY;
                     const T *in = st_base[u] + hin;
                     const T2 *ys = ys_base[u];
-                    const T2 cy = ys[(0 * R + ir) * W_IN];
-                    const T2 vy = ys[(1 * R + ir) * W_IN];
+                    const T2 cy = ys[ir * W_IN];
+                    const T2 vy = ys[YSLOT + ir * W_IN];
                     const T m0 = cy.x, s0 = cy.y;
                     T h = in[(0 * R + ir) * W_IN];
                     T p = in[(2 * R + ir) * W_IN];
@@ -674,7 +699,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     } else {
                         vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h, px, Y.ws4, Y.wc4);  // V_X  (row R-4)
                         vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs4, Y.vc4);   // V_Y  (row R-4)
-                        const T2 vx = ys[(2 * R + ir) * W_IN];
+                        const T2 vx = ys[2 * YSLOT + ir * W_IN];
                         Y.wc4 = Y.wc3; Y.ws4 = Y.ws3; Y.wc3 = Y.wc2; Y.ws3 = Y.ws2;
                         Y.wc2 = Y.wc1; Y.ws2 = Y.ws1; Y.wc1 = vx.x; Y.ws1 = vx.y;
                     }
@@ -721,10 +746,10 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
     const CUtensorMap *tcf = prm.tma ? &prm.tm_coef : nullptr;
     if (prm.a.fam0 + int(blockIdx.z) == 0)
         sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf, &prm.tm_state_r,
-                                                &prm.tm_coef_r);
+                                                &prm.tm_coef_r, prm.merged ? &prm.tm_coef_m : nullptr);
     else
         sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf, &prm.tm_state_r,
-                                                &prm.tm_coef_r);
+                                                &prm.tm_coef_r, prm.merged ? &prm.tm_coef_m : nullptr);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -749,7 +774,7 @@ inline EncodeTiledFn encode_tiled_fn() {
 
 // Tensor maps of one FP32 pass (see SweepParams); false when TMA cannot be used
 // (Nx not a multiple of 8, no encoder), in which case the kernel copies with cp.async.
-inline bool make_sweep_maps(const SweepArgs &a, int R, SweepParams &prm) {
+inline bool make_sweep_maps(const SweepArgs &a, int K, int R, SweepParams &prm) {
     const EncodeTiledFn fn = encode_tiled_fn();
     if (!fn || a.Nx % 8 != 0) return false;
     const cuuint64_t Nx = cuuint64_t(a.Nx), Ny = cuuint64_t(a.Ny);
@@ -774,6 +799,17 @@ inline bool make_sweep_maps(const SweepArgs &a, int R, SweepParams &prm) {
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
+    const cuuint64_t G = cuuint64_t(R + 4);
+    prm.merged = 0;
+    if (K > 1 && Ny % G == 0) {
+        const cuuint32_t one5[5] = {1, 1, 1, 1, 1};
+        const cuuint64_t mdim[5] = {16, Nx / 8, G, Ny / G, cuuint64_t(NPAIR)};
+        const cuuint64_t mstr[4] = {64, Nx * 8, G * Nx * 8, Nx * Ny * 8};
+        const cuuint32_t mbox[5] = {16, 32, cuuint32_t(R), cuuint32_t(K), 1};
+        prm.merged = fn(&prm.tm_coef_m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(a.coef), mdim, mstr,
+                        mbox, one5, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     return fn(&prm.tm_coef, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, cbox, one,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -810,7 +846,7 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     SweepParams prm;
     memset(&prm, 0, sizeof(prm));
     prm.a = a;
-    if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, R, prm)) ? 1 : 0;
+    if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, K, R, prm)) ? 1 : 0;
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
     dim3 grid(nsx, ncy, nfam);
