@@ -30,13 +30,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes per sweep launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on the default workload; valid only for the kernel source it was measured on
-# (profiles/sweep_kernel_cylinders8192_launches.md).
-# DRAM bytes per sweep launch from one ncu capture (profiles/sweep_kernel_cylinders8192_launches.md), valid
-# while the sweep's code (comment lines excluded), the workload, steps per pass and rows per tile match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "94dfb3fc4ff6ba65", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 4, "chunk_rows": 1024, "bytes_per_launch": 5.701e9 + 1.593e9}
+# DRAM bytes per sweep launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
+# excluded), the workload, steps per pass and rows per tile match.
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "1017c91b72cebb6b", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 2, "chunk_rows": 320, "bytes_per_launch": 5.977e9 + 1.594e9}
 
 METRIC = "site-updates/s per QLA step"
 UNIT = "site-updates/s"

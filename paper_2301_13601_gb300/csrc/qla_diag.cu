@@ -4,7 +4,7 @@
 // scheduling).
 //
 // Pass 1 (diag_partial): block b takes rows b, b + G, b + 2G, ...; every
-// thread keeps compensated sums over its sites; the block combines its
+// thread keeps compensated sums of its per-row sums; the block combines its
 // threads in a fixed tree and writes one partial record to scratch.
 // Pass 2 (diag_final): one block combines the G partials in a fixed tree.
 #include <math.h>
@@ -46,33 +46,41 @@ template <typename T>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_partial(const T *__restrict__ q, int Nx, int Ny,
                                                              Partial *__restrict__ part) {
     const size_t P = size_t(Nx) * size_t(Ny);
-    const T *q3 = q + 3 * P, *q4 = q + 4 * P, *q5 = q + 5 * P;
+    const T *q3 = q + 3 * P, *q4 = q + 4 * P;
     CSum e{0.0, 0.0}, d{0.0, 0.0};
-    double dmax = 0.0, bmax = 0.0;
+    double dmax = 0.0, b2max = 0.0;
     unsigned long long nf = 0;
     for (int y = blockIdx.x; y < Ny; y += gridDim.x) {
         const int yp = y + 1 == Ny ? 0 : y + 1, ym = y == 0 ? Ny - 1 : y - 1;
         const size_t r = size_t(y) * Nx;
+        // A thread's sites of one row (at most ceil(Nx / DIAG_THREADS) terms of
+        // equal sign) are summed plainly in FP64; the row sums enter the
+        // compensated sums. The FP64 pipe is the bound of this kernel, so
+        // per-site work is kept to the squares and one add per sum.
+        double erow = 0.0, drow = 0.0;
         for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
             const size_t i = r + x;
-            double site = 0.0;
+            double sq[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 const T v = q[size_t(c) * P + i];
                 if (!finite_val(v)) ++nf;
                 const double dv = double(v);
-                site += dv * dv;
+                sq[c] = dv * dv;
             }
-            e.add(site);
+            const double b2 = sq[3] + sq[4] + sq[5];
+            erow += (sq[0] + sq[1] + sq[2]) + b2;
+            b2max = fmax(b2max, b2);
             const int xp = x + 1 == Nx ? 0 : x + 1, xm = x == 0 ? Nx - 1 : x - 1;
             const double dv = 0.5 * (double(q3[r + xp]) - double(q3[r + xm])) +
                               0.5 * (double(q4[size_t(yp) * Nx + x]) - double(q4[size_t(ym) * Nx + x]));
-            d.add(dv * dv);
+            drow = fma(dv, dv, drow);
             dmax = fmax(dmax, fabs(dv));
-            const double b3 = double(q3[i]), b4 = double(q4[i]), b5 = double(q5[i]);
-            bmax = fmax(bmax, sqrt(b3 * b3 + b4 * b4 + b5 * b5));
         }
+        e.add(erow);
+        d.add(drow);
     }
+    const double bmax = sqrt(b2max);  // sqrt is monotonic: the max of the site norms
     __shared__ Partial sh[DIAG_THREADS];
     sh[threadIdx.x] = Partial{e.s, e.c, d.s, d.c, dmax, bmax, nf, 0ull};
     __syncthreads();
