@@ -27,10 +27,19 @@ struct BatchInst {
     void *q[2];
     const void *coef;
     int Nx, Ny, w_valid, chunk, nsx, ncy, tiles, passes, vec;
+    int tma, merged;  // tensor maps encoded (see BatchMaps); merged-level coefficient map encoded
+};
+
+// TMA tensor maps of one instance (as SweepParams, for both state buffers),
+// kept in device memory and read by the TMA unit from there.
+struct BatchMaps {
+    CUtensorMap st[2], st_r[2];
+    CUtensorMap cf, cf_r, cf_m;
 };
 
 struct BatchSched {
     const BatchInst *inst;           // sorted by passes, descending
+    const BatchMaps *maps;           // [ninst], same order
     int ninst;
     int maxpass;
     const long long *pass_start;     // [maxpass + 1]
@@ -60,7 +69,11 @@ template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB)
     batch_kernel(const BatchSched S) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ int sh[6];  // stop, instance, pass, family, strip, chunk
+    // stop, instance, pass, family, strip, chunk: after the sweep's layout in
+    // the dynamic allocation (a static array would shift the 1024-byte aligned
+    // dynamic base by a whole kilobyte)
+    using L = SweepLayout<T, K, R, INTER>;
+    int *const sh = reinterpret_cast<int *>(smem_raw + L::SMEM);
     for (;;) {
         if (threadIdx.x == 0) {
             int stop = 0, inst = 0, pass = 0, fam = 0, tile = 0;
@@ -130,9 +143,19 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
         a.unitary = UNIT ? 1 : 0;
         a.vec = I.vec;
         a.fam0 = 0;
-        a.error = nullptr;  // the batch copies with cp.async (no TMA waits)
-        if (fam == 0) sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, chunk, smem_raw);
-        else sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, chunk, smem_raw);
+        a.error = S.error;  // a TMA wait that runs out stops the batch like a dependency timeout
+        const BatchMaps *M = I.tma ? &S.maps[inst] : nullptr;
+        // the input rows were written by other CTAs (generic proxy) and are
+        // read here by TMA loads (async proxy)
+        asm volatile("fence.proxy.async;\n" ::: "memory");
+        if (fam == 0)
+            sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, chunk, smem_raw, M ? &M->st[par] : nullptr,
+                                                    M ? &M->cf : nullptr, M ? &M->st_r[par] : nullptr,
+                                                    M ? &M->cf_r : nullptr, M && I.merged ? &M->cf_m : nullptr);
+        else
+            sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, chunk, smem_raw, M ? &M->st[par] : nullptr,
+                                                    M ? &M->cf : nullptr, M ? &M->st_r[par] : nullptr,
+                                                    M ? &M->cf_r : nullptr, M && I.merged ? &M->cf_m : nullptr);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -148,18 +171,25 @@ __global__ void batch_flip(const BatchInst *inst, int *cur, int n) {
     if (i < n) cur[i] ^= (inst[i].passes & 1);
 }
 
+constexpr int kBatchRows = 4;  // rows per iteration of the batch's sweep configurations (K = 2 and 4)
+
+// dynamic shared memory of the batch kernel: the sweep's layout + 6 scheduler words
+template <int K, int R, bool INTER>
+constexpr size_t batch_smem() {
+    return SweepLayout<float, K, R, INTER>::SMEM + 32;
+}
+
 // Sets the shared-memory attribute and returns the persistent grid size
 // (SMs x resident CTAs); called before stream capture.
 template <int K, int R, int NY, bool INTER, bool UNIT>
 cudaError_t prepare_batch_t(int sms, int *grid) {
     using Cfg = SweepCfg<float, K, R, NY>;
-    using L = SweepLayout<float, K, R, INTER>;
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<float, K, R, NY, INTER, UNIT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::SMEM));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem<K, R, INTER>()));
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<float, K, R, NY, INTER, UNIT>, Cfg::NT,
-                                                      L::SMEM);
+                                                      batch_smem<K, R, INTER>());
     if (e != cudaSuccess) return e;
     *grid = sms * (occ < 1 ? 1 : occ);
     return cudaSuccess;
@@ -168,8 +198,7 @@ cudaError_t prepare_batch_t(int sms, int *grid) {
 template <int K, int R, int NY, bool INTER, bool UNIT>
 cudaError_t launch_batch_t(const BatchSched &S, int grid, cudaStream_t st) {
     using Cfg = SweepCfg<float, K, R, NY>;
-    using L = SweepLayout<float, K, R, INTER>;
-    batch_kernel<float, K, R, NY, INTER, UNIT><<<grid, Cfg::NT, L::SMEM, st>>>(S);
+    batch_kernel<float, K, R, NY, INTER, UNIT><<<grid, Cfg::NT, batch_smem<K, R, INTER>(), st>>>(S);
     return cudaGetLastError();
 }
 
@@ -187,8 +216,8 @@ cudaError_t batch_modes(bool inter, bool unit, int sms, int *grid, const BatchSc
 // S == nullptr: prepare (attribute + grid size); otherwise launch with *grid CTAs.
 cudaError_t batch_dispatch(int K, bool inter, bool unit, int sms, int *grid, const BatchSched *S, cudaStream_t st) {
     switch (K) {
-        case 2: return batch_modes<2, 4, 2>(inter, unit, sms, grid, S, st);
-        case 4: return batch_modes<4, 4, 2>(inter, unit, sms, grid, S, st);
+        case 2: return batch_modes<2, kBatchRows, 2>(inter, unit, sms, grid, S, st);
+        case 4: return batch_modes<4, kBatchRows, 2>(inter, unit, sms, grid, S, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -212,6 +241,7 @@ struct qla_batch {
     std::vector<int> cur;              // host copy of the parities
     std::vector<void *> allocs;
     qla::BatchInst *d_inst = nullptr;
+    qla::BatchMaps *d_maps = nullptr;
     long long *d_pass_start = nullptr;
     int *d_active = nullptr;
     long long *d_tile_prefix = nullptr;
@@ -348,6 +378,35 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
         cudaFree(idx);
         b->allocs.pop_back();
     }
+    // TMA tensor maps of every instance (both state buffers); an instance whose
+    // maps cannot be encoded copies with cp.async
+    std::vector<qla::BatchMaps> maps(count);
+    for (int k = 0; k < count; ++k) {
+        qla::BatchInst &I = b->inst[k];
+        bool ok = true;
+        for (int par = 0; par < 2 && ok; ++par) {
+            qla::SweepArgs a;
+            memset(&a, 0, sizeof(a));
+            a.q_in = I.q[par];
+            a.coef = I.coef;
+            a.Nx = I.Nx;
+            a.Ny = I.Ny;
+            a.w_valid = I.w_valid;
+            a.chunk = I.chunk;
+            qla::SweepParams prm;
+            memset(&prm, 0, sizeof(prm));
+            ok = qla::make_sweep_maps(a, K, qla::kBatchRows, prm);
+            maps[k].st[par] = prm.tm_state;
+            maps[k].st_r[par] = prm.tm_state_r;
+            if (par == 0) {
+                maps[k].cf = prm.tm_coef;
+                maps[k].cf_r = prm.tm_coef_r;
+                maps[k].cf_m = prm.tm_coef_m;
+                I.merged = prm.merged;
+            }
+        }
+        I.tma = ok ? 1 : 0;
+    }
     // schedule tables
     b->maxpass = b->inst[0].passes;
     std::vector<long long> tile_prefix(count + 1, 0);
@@ -362,6 +421,7 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
     }
     b->total_items = pass_start[b->maxpass];
     if (dalloc(b, &b->d_inst, sizeof(qla::BatchInst) * count) != cudaSuccess ||
+        dalloc(b, &b->d_maps, sizeof(qla::BatchMaps) * count) != cudaSuccess ||
         dalloc(b, &b->d_pass_start, sizeof(long long) * (b->maxpass + 1)) != cudaSuccess ||
         dalloc(b, &b->d_active, sizeof(int) * active.size()) != cudaSuccess ||
         dalloc(b, &b->d_tile_prefix, sizeof(long long) * (count + 1)) != cudaSuccess ||
@@ -373,6 +433,7 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
     if (cudaMallocHost(reinterpret_cast<void **>(&b->h_diag), sizeof(qla::DiagResult)) != cudaSuccess)
         return bail(QLA_ENOMEM);
     if (cudaMemcpy(b->d_inst, b->inst.data(), sizeof(qla::BatchInst) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_maps, maps.data(), sizeof(qla::BatchMaps) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_pass_start, pass_start.data(), sizeof(long long) * pass_start.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(b->d_active, active.data(), sizeof(int) * active.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -392,6 +453,7 @@ qla_status qla_batch_run(qla_batch *b) {
     if (!b->exec) {
         qla::BatchSched S;
         S.inst = b->d_inst;
+        S.maps = b->d_maps;
         S.ninst = b->n;
         S.maxpass = b->maxpass;
         S.pass_start = b->d_pass_start;
