@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 MEASURED_TRAFFIC = {"sweep_sha256_prefix": "1017c91b72cebb6b", "workload": "cylinders8192_fp32",
                     "steps_per_pass": 2, "chunk_rows": 320, "bytes_per_launch": 5.977e9 + 1.594e9}
 
+L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"
 UNIT = "site-updates/s"
 BYTES_PER_SITE_UPDATE = 60.0  # FP32 general kernel: 24 B state read + 24 B write + 12 B n_x, n_y, n_z
@@ -300,7 +301,9 @@ def run_ours(args):
         "config": {"workload": w.name, "lattice": f"{w.Nx}x{w.Ny}", "delta": w.delta,
                    "qla_steps_per_bench_step": S, "steps_per_pass": k, "chunk_rows": sim.chunk_rows,
                    "precision": "fp32", "sequence": "interleaved", "potential": "paper",
-                   "l2": "inputs larger than L2 (state 1.6 GB)", "parallelism": f"replicas x{world}"},
+                   "l2": (f"inputs {'larger' if 80 * sites > L2_BYTES else 'smaller'} than L2 (state "
+                          f"{24 * sites / 1e9:.2f} GB + coefficients {56 * sites / 1e9:.2f} GB read per pass)"),
+                   "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": f"sweep_kernel<float,{k}>", "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
