@@ -95,6 +95,23 @@ def test_fp32_tma_strips_match_oracle(K, sequence, potential):
     assert rel_l2(got, ref) < 3e-6
 
 
+@pytest.mark.parametrize("K", [2, 4])
+@pytest.mark.parametrize("Ny, chunk", [(100, 40), (96, 37), (98, 24)])
+def test_fp32_tma_block_boxes_match_oracle(K, Ny, chunk):
+    """The TMA copies load whole R-row blocks, and one box for the blocks of
+    all levels of a coefficient plane when they lie in one group of R + 4
+    rows. Cases: Ny not a multiple of R + 4 (no merged view: one box per
+    level), tiles of 37 rows (level blocks straddling a row group in every
+    other iteration), Ny not a multiple of R (blocks at the y-wrap loaded
+    row by row)."""
+    Nx = 1024
+    n, q0 = problem(Nx, Ny, seed=7)
+    delta, steps = 0.2, 3 * K + 1
+    got = gpu_run(n, q0, delta, steps, precision="fp32", steps_per_pass=K, chunk_rows=chunk)
+    ref = oracle_run(n, q0, delta, steps, "interleaved", "paper")
+    assert rel_l2(got, ref) < 3e-6
+
+
 def test_pulse_init_matches_oracle():
     for pol, name in ((0, "Ez"), (1, "Ey")):
         Nx, Ny = 300, 20
