@@ -241,8 +241,9 @@ typedef struct {
 qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla_options *opt, qla_batch **out);
 
 /* Advance every lattice by its nsteps (one graph launch; blocks until done).
- * QLA_ETIMEOUT if a dependency wait exceeded its limit (the states are then
- * partially advanced and should be discarded). */
+ * QLA_ETIMEOUT if a dependency wait or a tile's wait for its TMA copies
+ * exceeded its limit (the states are then partially advanced and should be
+ * discarded). */
 qla_status qla_batch_run(qla_batch *b);
 
 /* State of lattice i (creation order) as a host float array [6][Ny][Nx]. */

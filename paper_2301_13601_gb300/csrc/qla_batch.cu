@@ -495,7 +495,7 @@ qla_status qla_batch_run(qla_batch *b) {
         return QLA_ECUDA;
     for (int k = 0; k < b->n; ++k) b->cur[k] ^= (b->inst[k].passes & 1);
     if (err) {
-        b->msg = "a dependency wait timed out";
+        b->msg = "a dependency wait or a TMA copy wait timed out";
         return QLA_ETIMEOUT;
     }
     return QLA_OK;
