@@ -315,11 +315,49 @@ def run_ours(args):
         "gpu_launches": args.steps * (launches_per_step + 2),
         "energy_last": last["energy"] if last else None,
     }
+    if not args.skip_extras:
+        line["single_family"] = single_family_report(w, args, peak, peak_kind)
     if not args.skip_extras and not args.skip_surrogate:
         line["surrogate"] = surrogate_report()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def single_family_report(w, args, peak, peak_kind, steps: int = 5):
+    """The same workload with only the pulse's polarisation family stored and
+    advanced (qla_options.families): the other family's three components are
+    zero at the start and stay exactly zero under every operator, so the result
+    is the same state (bit for bit, tested) for half the work. Its algorithmic
+    bytes per site-update are those of the family's kernel (TM: 24 B of state +
+    4 B of n_z; TE: 24 B + 8 B of n_x, n_y)."""
+    import torch
+
+    from paper_2301_13601_gb300 import media
+    from paper_2301_13601_gb300.qla import Simulation
+
+    fam, pol = ("TM", "Ez") if w.pulse.pol == media.POL_EZ else ("TE", "Ey")
+    alg = 28.0 if fam == "TM" else 32.0
+    S = QLA_STEPS_PER_BENCH_STEP
+    with Simulation(*w.medium(), w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
+                    chunk_rows=args.chunk_rows, families=fam) as sim:
+        sim.init_pulse(pol, w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+        sim.step(S)
+        sim.diagnostics()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        for _ in range(steps):
+            sim.step(S)
+            sim.diagnostics()
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    value = w.Nx * w.Ny * S / (ms / 1e3)
+    return {"families": fam, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "bytes_per_site_update": alg, "bandwidth_equivalent_frac": value * alg / 1e9 / peak,
+            "peak_kind": peak_kind, "note": "same bench step (100 QLA steps + diagnostics); the other family's "
+            "planes are zero and stay zero (Eq. 17-22 never couple the families)"}
 
 
 SURROGATE_CHECKPOINT = os.path.join(ROOT, "paper_2301_13601_gb300", "checkpoints", "surrogate_k16.npz")

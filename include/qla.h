@@ -52,6 +52,14 @@ enum { QLA_FP32 = 0, QLA_FP64 = 1 };                        /* state / arithmeti
 enum { QLA_SEQ_INTERLEAVED = 0, QLA_SEQ_PLAIN = 1 };        /* Eq. 28 / Eq. 23 */
 enum { QLA_POT_PAPER = 0, QLA_POT_UNITARY = 1 };            /* V as printed / unitary variant */
 enum { QLA_POL_EZ = 0, QLA_POL_EY = 1 };                    /* pulse polarisation */
+/* Polarisation families advanced (qla_options.families). The six components
+ * split into two families that no operator of Eq. 17-22 couples (C_X pairs
+ * (q1,q5), (q2,q4); C_Y (q0,q5), (q2,q3); the potential rows 5<-1, 4<-2,
+ * 3<-2, 5<-0): TM = (q2, q3, q4) = (n_z E_z, B_x, B_y), the E_z polarisation;
+ * TE = (q0, q1, q5) = (n_x E_x, n_y E_y, B_z), the E_y polarisation. A field
+ * with only one family's components nonzero keeps the other family at exactly
+ * zero, so advancing one family gives the same result at half the work. */
+enum { QLA_FAMILIES_BOTH = 0, QLA_FAMILY_TM = 1, QLA_FAMILY_TE = 2 };
 
 /* Options for qla_create. Obtain defaults with qla_default_options().
  * potential: QLA_POT_PAPER applies V_X, V_Y as printed (Eq. 21-22, with
@@ -69,6 +77,10 @@ typedef struct {
                             pass, 1024 otherwise), else >= 8 */
     int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
     void *stream;        /* cudaStream_t to run on; NULL = a non-blocking stream owned by the context */
+    int families;        /* QLA_FAMILIES_BOTH (default), or QLA_FAMILY_TM / QLA_FAMILY_TE: only that
+                            family is stored and advanced; the other family's components are
+                            held at zero (qla_set_fields* ignore them, qla_get_fields* return
+                            zeros, qla_init_pulse requires the matching polarisation) */
 } qla_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -116,11 +128,13 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
  *   g(x) = amplitude * exp(-d^2 / (2 sigma^2)),  d = periodic minimum-image x - x0,
  *   QLA_POL_EZ: q2 = g, q4 = -g;  QLA_POL_EY: q1 = g, q5 = +g;  others 0.
  * (the pairings follow the +x travelling solution of Eq. 16 in a uniform medium).
- * Resets the step counter. Errors: QLA_EINVAL (sigma <= 0, bad polarisation). */
+ * Resets the step counter. Errors: QLA_EINVAL (sigma <= 0, bad polarisation,
+ * or a polarisation whose family the context does not advance). */
 qla_status qla_init_pulse(qla_ctx *ctx, int polarization, double x0, double sigma, double amplitude);
 
 /* Copy a host state [6][Ny][Nx] (double) into the context (rounded to the
- * context precision). Resets the step counter. Synchronous. */
+ * context precision). Resets the step counter. Synchronous. With a single
+ * family (qla_options.families) only that family's three planes are copied. */
 qla_status qla_set_fields(qla_ctx *ctx, const double *q);
 
 /* Same with a float host state [6][Ny][Nx]; no rounding in FP32 mode.
@@ -187,7 +201,8 @@ qla_status qla_get_fields(qla_ctx *ctx, double *q);
 qla_status qla_get_fields_f32(qla_ctx *ctx, float *q);
 
 /* Device pointer to the current state (6 planes [6][Ny][Nx] of float or
- * double, per the precision). Valid until the next qla_step. */
+ * double, per the precision). Valid until the next qla_step. With a single
+ * family, writes through it must leave the other family's planes zero. */
 void *qla_state_device_ptr(qla_ctx *ctx);
 
 /* Block the host until all queued work of the context has finished.
@@ -237,7 +252,8 @@ typedef struct {
  * read during the call). opt: precision must be QLA_FP32; steps_per_pass 2 or 4
  * (0 = 4); sequence and potential apply to every lattice; opt->stream is
  * ignored (the batch owns a stream). Errors: QLA_EINVAL (bad descriptor),
- * QLA_EUNSUPPORTED (precision or steps_per_pass), QLA_ENOMEM, QLA_ECUDA. */
+ * QLA_EUNSUPPORTED (precision, steps_per_pass, or opt->families other than
+ * QLA_FAMILIES_BOTH), QLA_ENOMEM, QLA_ECUDA. */
 qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla_options *opt, qla_batch **out);
 
 /* Advance every lattice by its nsteps (one graph launch; blocks until done).

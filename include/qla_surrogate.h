@@ -139,7 +139,9 @@ enum {
  * E_ref (e.g. the energy at the start of an earlier rollout segment);
  * otherwise E_ref is measured on the context's state at the start.
  * n: device FP32 [3][Ny][Nx]. The surrogate must have nimg == 1 and the
- * context's lattice. Runs on the context's stream; synchronous. */
+ * context's lattice, and the context must advance both polarisation families
+ * (QLA_EUNSUPPORTED otherwise: the network writes all six components). Runs
+ * on the context's stream; synchronous. */
 qla_status qla_surrogate_rollout(qla_surrogate *s, qla_ctx *ctx, const float *n, int calls, double drift_tol,
                                  int drift_mode, double energy_ref, qla_rollout_stats *stats);
 

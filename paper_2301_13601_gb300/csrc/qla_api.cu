@@ -141,6 +141,14 @@ int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
     return std::max(1, best_chunk);
 }
 
+// Whether component `comp` (Eq. 15 order) belongs to a family the context
+// advances: TM = (q2, q3, q4), TE = (q0, q1, q5).
+bool family_has(const qla_ctx *c, int comp) {
+    if (c->opt.families == QLA_FAMILIES_BOTH) return true;
+    const bool tm = comp >= 2 && comp <= 4;
+    return c->opt.families == QLA_FAMILY_TM ? tm : !tm;
+}
+
 qla_status launch_pass(qla_ctx *c, int K) {
     qla::SweepArgs a{};
     a.q_in = c->state[c->cur];
@@ -153,10 +161,13 @@ qla_status launch_pass(qla_ctx *c, int K) {
     a.interleaved = c->opt.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0;
     a.unitary = c->opt.potential == QLA_POT_UNITARY ? 1 : 0;
     a.vec = (c->Nx % int(16 / c->esize)) == 0 ? 1 : 0;
-    a.fam0 = 0;
+    // one CTA grid layer per advanced family (TM = family 0, TE = family 1);
+    // the planes of a family that is not advanced stay zero in both buffers
+    const int nfam = c->opt.families == QLA_FAMILIES_BOTH ? 2 : 1;
+    a.fam0 = c->opt.families == QLA_FAMILY_TE ? 1 : 0;
     a.error = c->sweep_err;
-    cudaError_t e = c->opt.precision == QLA_FP64 ? qla::launch_sweep_f64(K, a, 2, c->stream)
-                                                  : qla::launch_sweep_f32(K, a, 2, c->stream);
+    cudaError_t e = c->opt.precision == QLA_FP64 ? qla::launch_sweep_f64(K, a, nfam, c->stream)
+                                                  : qla::launch_sweep_f32(K, a, nfam, c->stream);
     if (e != cudaSuccess) return fail(c, QLA_ECUDA, "sweep launch (K=%d): %s", K, cudaGetErrorString(e));
     c->cur ^= 1;
     return QLA_OK;
@@ -195,6 +206,7 @@ void qla_default_options(qla_options *opt) {
     opt->chunk_rows = 0;
     opt->device = -1;
     opt->stream = nullptr;
+    opt->families = QLA_FAMILIES_BOTH;
 }
 
 qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_buffer_sizes *out) {
@@ -223,6 +235,8 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
     if (o.precision != QLA_FP32 && o.precision != QLA_FP64) return QLA_EINVAL;
     if (o.sequence != QLA_SEQ_INTERLEAVED && o.sequence != QLA_SEQ_PLAIN) return QLA_EINVAL;
     if (o.potential != QLA_POT_PAPER && o.potential != QLA_POT_UNITARY) return QLA_EINVAL;
+    if (o.families != QLA_FAMILIES_BOTH && o.families != QLA_FAMILY_TM && o.families != QLA_FAMILY_TE)
+        return QLA_EINVAL;
     if (o.steps_per_pass < 0 || o.chunk_rows < 0) return QLA_EINVAL;
     if (o.steps_per_pass > 0 && !qla::sweep_supported(o.precision, o.steps_per_pass)) return QLA_EUNSUPPORTED;
     const size_t P = size_t(Nx) * size_t(Ny);
@@ -312,6 +326,9 @@ qla_status qla_init_pulse(qla_ctx *c, int polarization, double x0, double sigma,
     if ((polarization != QLA_POL_EZ && polarization != QLA_POL_EY) || !(sigma > 0.0) || !std::isfinite(x0) ||
         !std::isfinite(sigma) || !std::isfinite(amplitude))
         return fail(c, QLA_EINVAL, "qla_init_pulse: invalid argument");
+    if ((polarization == QLA_POL_EZ && c->opt.families == QLA_FAMILY_TE) ||
+        (polarization == QLA_POL_EY && c->opt.families == QLA_FAMILY_TM))
+        return fail(c, QLA_EINVAL, "qla_init_pulse: the pulse's family is not advanced by this context");
     cudaError_t e = qla::launch_init_pulse(c->state[c->cur], c->Nx, c->Ny, c->opt.precision == QLA_FP64 ? 1 : 0,
                                            polarization, x0, sigma, amplitude, c->stream);
     if (e != cudaSuccess) return fail(c, QLA_ECUDA, "pulse launch: %s", cudaGetErrorString(e));
@@ -324,13 +341,20 @@ qla_status qla_set_fields(qla_ctx *c, const double *q) {
     qla_status s = enter(c);
     if (s != QLA_OK) return s;
     if (!q) return fail(c, QLA_EINVAL, "qla_set_fields: NULL");
-    const size_t n = 6 * size_t(c->Nx) * size_t(c->Ny);
-    if (c->opt.precision == QLA_FP64) {
-        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], q, n * 8, cudaMemcpyHostToDevice, c->stream));
-    } else {
-        std::vector<float> tmp(n);
-        for (size_t i = 0; i < n; ++i) tmp[i] = float(q[i]);
-        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], tmp.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    const size_t P = size_t(c->Nx) * size_t(c->Ny);
+    std::vector<float> tmp(c->opt.precision == QLA_FP64 ? 0 : P);
+    for (int comp = 0; comp < 6; ++comp) {
+        if (!family_has(c, comp)) continue;
+        const double *src = q + comp * P;
+        if (c->opt.precision == QLA_FP64) {
+            QLA_CUDA(c, cudaMemcpyAsync(static_cast<double *>(c->state[c->cur]) + comp * P, src, P * 8,
+                                        cudaMemcpyHostToDevice, c->stream));
+        } else {
+            QLA_CUDA(c, cudaStreamSynchronize(c->stream));  // tmp is reused per plane
+            for (size_t i = 0; i < P; ++i) tmp[i] = float(src[i]);
+            QLA_CUDA(c, cudaMemcpyAsync(static_cast<float *>(c->state[c->cur]) + comp * P, tmp.data(), P * 4,
+                                        cudaMemcpyHostToDevice, c->stream));
+        }
     }
     QLA_CUDA(c, cudaStreamSynchronize(c->stream));
     c->steps = 0;
@@ -342,14 +366,25 @@ qla_status qla_set_fields_f32(qla_ctx *c, const float *q) {
     qla_status s = enter(c);
     if (s != QLA_OK) return s;
     if (!q) return fail(c, QLA_EINVAL, "qla_set_fields_f32: NULL");
-    const size_t n = 6 * size_t(c->Nx) * size_t(c->Ny);
+    const size_t P = size_t(c->Nx) * size_t(c->Ny);
     if (c->opt.precision == QLA_FP32) {
-        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], q, n * 4, cudaMemcpyHostToDevice, c->stream));
+        if (c->opt.families == QLA_FAMILIES_BOTH) {
+            QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], q, 6 * P * 4, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            for (int comp = 0; comp < 6; ++comp)
+                if (family_has(c, comp))
+                    QLA_CUDA(c, cudaMemcpyAsync(static_cast<float *>(c->state[c->cur]) + comp * P, q + comp * P,
+                                                P * 4, cudaMemcpyHostToDevice, c->stream));
+        }
     } else {
-        std::vector<double> tmp(n);
-        for (size_t i = 0; i < n; ++i) tmp[i] = double(q[i]);
-        QLA_CUDA(c, cudaMemcpyAsync(c->state[c->cur], tmp.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
-        QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+        std::vector<double> tmp(P);
+        for (int comp = 0; comp < 6; ++comp) {
+            if (!family_has(c, comp)) continue;
+            for (size_t i = 0; i < P; ++i) tmp[i] = double(q[comp * P + i]);
+            QLA_CUDA(c, cudaMemcpyAsync(static_cast<double *>(c->state[c->cur]) + comp * P, tmp.data(), P * 8,
+                                        cudaMemcpyHostToDevice, c->stream));
+            QLA_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
     }
     c->steps = 0;
     c->has_state = true;
@@ -506,6 +541,7 @@ bool ctx_view(qla_ctx *c, CtxView *v) {
     v->cur_state = c->state[c->cur];
     v->spare_state = c->state[c->cur ^ 1];
     v->has_state = c->has_state ? 1 : 0;
+    v->families = c->opt.families;
     return true;
 }
 

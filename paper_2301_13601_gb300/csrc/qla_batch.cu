@@ -290,7 +290,7 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
     qla_options o;
     qla_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != QLA_FP32) return QLA_EUNSUPPORTED;
+    if (o.precision != QLA_FP32 || o.families != QLA_FAMILIES_BOTH) return QLA_EUNSUPPORTED;
     const int K = o.steps_per_pass > 0 ? o.steps_per_pass : 4;
     if (K != 2 && K != 4) return QLA_EUNSUPPORTED;
     for (int i = 0; i < count; ++i) {

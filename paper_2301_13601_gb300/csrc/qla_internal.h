@@ -140,6 +140,7 @@ struct CtxView {
     void *cur_state;     // current state [6][Ny][Nx]
     void *spare_state;   // the other state buffer (free between steps)
     int has_state;
+    int families;        // QLA_FAMILIES_BOTH, QLA_FAMILY_TM or QLA_FAMILY_TE
 };
 bool ctx_view(qla_ctx *c, CtxView *v);
 // The spare buffer, now holding the state `steps` steps later, becomes current.

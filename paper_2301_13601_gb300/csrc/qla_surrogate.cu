@@ -658,6 +658,8 @@ qla_status qla_surrogate_rollout(qla_surrogate *s, qla_ctx *ctx, const float *n,
         (drift_mode != QLA_DRIFT_PER_CALL && drift_mode != QLA_DRIFT_FROM_START))
         return sfail(s, QLA_EINVAL, "rollout: bad argument");
     if (v.precision != QLA_FP32) return sfail(s, QLA_EUNSUPPORTED, "rollout: the context must be FP32");
+    if (v.families != QLA_FAMILIES_BOTH)  // the network writes all six components
+        return sfail(s, QLA_EUNSUPPORTED, "rollout: the context must advance both families");
     if (s->cfg.nimg != 1 || v.Nx != s->cfg.W || v.Ny != s->cfg.H)
         return sfail(s, QLA_EINVAL, "rollout: lattice %dx%d does not match the surrogate's %dx%d (one image)", v.Nx,
                      v.Ny, s->cfg.W, s->cfg.H);

@@ -21,6 +21,7 @@ FP32, FP64 = 0, 1
 SEQ_INTERLEAVED, SEQ_PLAIN = 0, 1
 POT_PAPER, POT_UNITARY = 0, 1
 POL_EZ, POL_EY = 0, 1
+FAMILIES_BOTH, FAMILY_TM, FAMILY_TE = 0, 1, 2
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ENOMEM", 3: "QLA_ECUDA", 4: "QLA_ETIMEOUT",
           5: "QLA_ENONFINITE", 6: "QLA_EUNSUPPORTED", 7: "QLA_ESTATE"}
@@ -45,7 +46,7 @@ class QLAError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("sequence", ctypes.c_int), ("potential", ctypes.c_int),
                 ("steps_per_pass", ctypes.c_int), ("chunk_rows", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("families", ctypes.c_int)]
 
 
 class BufferSizes(ctypes.Structure):
@@ -146,7 +147,7 @@ class Simulation:
 
     def __init__(self, n_x, n_y, n_z, delta: float, precision="fp32", sequence="interleaved",
                  potential="paper", steps_per_pass: int = 0, chunk_rows: int = 0,
-                 device: Optional[int] = None, stream=None):
+                 device: Optional[int] = None, stream=None, families="both"):
         import torch  # device memory and streams
 
         if not torch.cuda.is_available():
@@ -174,6 +175,9 @@ class Simulation:
         opt.chunk_rows = int(chunk_rows)
         opt.device = dev
         opt.stream = ctypes.c_void_p(stream.cuda_stream)
+        # "TM": only (q2, q3, q4), the E_z polarisation; "TE": only (q0, q1, q5), E_y
+        opt.families = _code("families", {"both": FAMILIES_BOTH, "TM": FAMILY_TM, "TE": FAMILY_TE}, families)
+        self.families = families
         self.precision = opt.precision
         sizes = BufferSizes()
         self._check(L.qla_query_buffer_sizes(self.Nx, self.Ny, ctypes.byref(opt), ctypes.byref(sizes)),
