@@ -44,9 +44,10 @@ def single_key(Nx: int, Ny: int, precision: str, sequence: str, potential: str, 
 
 def chunk_candidates(Ny: int, K: int) -> List[int]:
     """Rows per tile to try: 0 (the library's wave-balancing choice) and a few
-    fixed heights between 16 K (warm-up at most a third) and the whole lattice."""
+    fixed heights between 16 K (warm-up at most a third) and the whole lattice
+    (finer around 256-512 rows, where two resident CTAs per SM measured best)."""
     out = {0}
-    for h in (128, 256, 512, 1024, 2048, 4096):
+    for h in (128, 192, 256, 320, 384, 512, 768, 1024, 2048, 4096):
         if 16 * K <= h < Ny:
             out.add(h)
     out.add(Ny)
