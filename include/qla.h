@@ -73,7 +73,7 @@ typedef struct {
     int potential;       /* QLA_POT_PAPER (default) or QLA_POT_UNITARY */
     int steps_per_pass;  /* full time steps fused per HBM pass: 0 = automatic (FP64: 2; FP32: 2 from
                             2^25 sites up, else 4), else 1, 2 or 4 */
-    int chunk_rows;      /* rows of one sweep tile: 0 = automatic (at most 384 rows at 2 steps a
+    int chunk_rows;      /* rows of one sweep tile: 0 = automatic (at most 256 rows at 2 steps a
                             pass, 1024 otherwise), else >= 8 */
     int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
     void *stream;        /* cudaStream_t to run on; NULL = a non-blocking stream owned by the context */

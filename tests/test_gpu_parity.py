@@ -262,7 +262,7 @@ def test_cylinders_8192_sampled_parity():
     n = w.medium()
     steps = 8  # four fused passes of 2 steps, the automatic configuration at this size
     with Simulation(*n, w.delta, precision="fp32") as sim:
-        assert sim.steps_per_pass == 2 and sim.chunk_rows <= 384
+        assert sim.steps_per_pass == 2 and sim.chunk_rows <= 256
         ch = sim.chunk_rows
         sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
         q0 = sim.get_fields()
