@@ -28,10 +28,11 @@
 //    coefficients of an iteration are copied into shared memory while the
 //    x-pass of that iteration runs, and the x-pass coefficients and next
 //    level-0 rows while the y-pass of the previous iteration runs. The copies
-//    are TMA tile loads (one row per load, mbarrier completion) where the strip
-//    does not wrap around x, per-lane cp.async elsewhere. (A bulk L2 prefetch
-//    two iterations ahead was measured to cost 18% on top of this staging and
-//    is not used.)
+//    are TMA tile loads where the strip does not wrap around x (one box per
+//    R-row block, or per coefficient plane for all levels; mbarrier
+//    completion), per-lane cp.async elsewhere. (A bulk L2 prefetch two
+//    iterations ahead was measured to cost 18% on top of this staging and is
+//    not used.)
 //  * Rotations use the (cos-1, sin) form h' = h + (m h + s p): one rounding at
 //    the scale of h per output, with coefficients whose FP32 norm error is
 //    minimised at creation. Coefficients are stored as (m, s) pairs.
