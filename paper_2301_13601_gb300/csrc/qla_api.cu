@@ -99,9 +99,11 @@ int sm_count(int dev) {
 
 // Default steps per pass. FP32: K = 2 (two CTAs per SM, 112 KB of shared
 // memory each) on lattices of at least 2^25 sites, else K = 4 (one 224 KB CTA
-// per SM). Measured on GB300, site-updates/s: 8192^2 K = 2 50.9 G vs K = 4
-// 45.2 G; 4096^2 41.1 G vs 42.5 G; 2048^2 30.4 G vs 34.2 G; 1024^2 19.3 G vs
-// 24.8 G: the second resident CTA pays only when there are enough tiles.
+// per SM). Measured on GB300, site-updates/s, K = 2 vs K = 4: 8192^2 64.3 G vs
+// 55.1 G; 6144^2 59.1 G vs 50.2 G; 4096^2 42.6-44.4 G vs 43.4-44.0 G (equal
+// within run-to-run spread); 3072^2 39.8 G vs 39.9 G; 2048^2 31.7 G vs 34.4 G;
+// 1024^2 19.9 G vs 25.4 G: the second resident CTA pays only when there are
+// enough tiles, and below that K = 4 halves the DRAM traffic.
 int default_steps_per_pass(int precision, int Nx, int Ny) {
     if (precision == QLA_FP64) return 2;
     return (long long)Nx * Ny >= (1LL << 25) ? 2 : 4;
