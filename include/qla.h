@@ -200,6 +200,31 @@ qla_status qla_diagnostics_noalloc(const void *q, int precision, int Nx, int Ny,
 qla_status qla_get_fields(qla_ctx *ctx, double *q);
 qla_status qla_get_fields_f32(qla_ctx *ctx, float *q);
 
+/* Single operators of one step, for operator-level tests (Sec. 3):
+ *   QLA_OP_CX, QLA_OP_CX_T: collision C_X (Eq. 17) on (q1,q5) by theta_1 and
+ *     (q2,q4) by theta_2, or its transpose;
+ *   QLA_OP_CY, QLA_OP_CY_T: C_Y (Eq. 19, row 2 read as (0,0,c2,s2,0,0)) on
+ *     (q0,q5) by theta_0 and (q2,q3) by theta_2, or its transpose;
+ *   QLA_OP_S14_XP .. QLA_OP_S25_YM: streaming S^{+x}_{14}, S^{-x}_{14},
+ *     S^{+x}_{25}, S^{-x}_{25}, S^{+y}_{03}, S^{-y}_{03}, S^{+y}_{25},
+ *     S^{-y}_{25} (Eq. 18, Eq. 20), with S^{+} q(r) <- q(r + e) and S^{-}
+ *     q(r) <- q(r - e), periodic;
+ *   QLA_OP_VX, QLA_OP_VY: the potentials (Eq. 21-22, the context's variant)
+ *     with the angles of one application in the context's step (beta for
+ *     Eq. 23, beta/2 for Eq. 28).
+ * The same per-site arithmetic and coefficients as qla_step. */
+enum {
+    QLA_OP_CX = 0, QLA_OP_CX_T = 1, QLA_OP_CY = 2, QLA_OP_CY_T = 3,
+    QLA_OP_S14_XP = 4, QLA_OP_S14_XM = 5, QLA_OP_S25_XP = 6, QLA_OP_S25_XM = 7,
+    QLA_OP_S03_YP = 8, QLA_OP_S03_YM = 9, QLA_OP_S25_YP = 10, QLA_OP_S25_YM = 11,
+    QLA_OP_VX = 12, QLA_OP_VY = 13
+};
+
+/* Apply operator `op` to the state `count` >= 0 times (asynchronous, on the
+ * context stream; the step counter is unchanged). Errors: QLA_EINVAL (unknown
+ * op, count < 0), QLA_ESTATE (no state), QLA_ECUDA. */
+qla_status qla_debug_apply(qla_ctx *ctx, int op, int count);
+
 /* Device pointer to the current state (6 planes [6][Ny][Nx] of float or
  * double, per the precision). Valid until the next qla_step. With a single
  * family, writes through it must leave the other family's planes zero. */

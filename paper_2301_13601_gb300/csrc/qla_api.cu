@@ -478,6 +478,22 @@ qla_status qla_get_fields_f32(qla_ctx *c, float *q) {
     return QLA_OK;
 }
 
+qla_status qla_debug_apply(qla_ctx *c, int op, int count) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (op < QLA_OP_CX || op > QLA_OP_VY || count < 0) return fail(c, QLA_EINVAL, "qla_debug_apply: bad op or count");
+    if (!c->has_state) return fail(c, QLA_ESTATE, "qla_debug_apply: no state");
+    for (int k = 0; k < count; ++k) {
+        bool swapped = false;
+        const cudaError_t e = qla::debug_apply(op, c->opt.precision, c->state[c->cur], c->state[c->cur ^ 1], c->coef,
+                                               c->Nx, c->Ny, c->opt.potential == QLA_POT_UNITARY ? 1 : 0, c->stream,
+                                               &swapped);
+        if (e != cudaSuccess) return fail(c, QLA_ECUDA, "qla_debug_apply: %s", cudaGetErrorString(e));
+        if (swapped) c->cur ^= 1;
+    }
+    return QLA_OK;
+}
+
 void *qla_state_device_ptr(qla_ctx *c) { return c ? c->state[c->cur] : nullptr; }
 
 qla_status qla_synchronize(qla_ctx *c) {

@@ -129,6 +129,11 @@ enum PackMode { PACK_PLAIN = 0, PACK_ADJOINT = 1, PACK_TIED_INPUT = 2 };
 cudaError_t launch_pack_weights(const float *w, int nout, int cin, int nout_pad, int cin_pad, int mode,
                                 void *packed, cudaStream_t st);
 
+// One operator of the step (qla_debug_apply), in place on `state` or, for a
+// streaming op, from `state` into `spare` (*swapped set).
+cudaError_t debug_apply(int op, int precision, void *state, void *spare, const void *coef, int Nx, int Ny, int unitary,
+                        cudaStream_t st, bool *swapped);
+
 }  // namespace qla
 
 // Access to a QLA context from other parts of the library (the surrogate

@@ -22,6 +22,10 @@ SEQ_INTERLEAVED, SEQ_PLAIN = 0, 1
 POT_PAPER, POT_UNITARY = 0, 1
 POL_EZ, POL_EY = 0, 1
 FAMILIES_BOTH, FAMILY_TM, FAMILY_TE = 0, 1, 2
+# single operators for qla_debug_apply: collisions (Eq. 17, Eq. 19), streaming
+# shifts S^{+-axis}_{components} (Eq. 18, Eq. 20), potentials (Eq. 21-22)
+OPS = {"CX": 0, "CX_T": 1, "CY": 2, "CY_T": 3, "S14+x": 4, "S14-x": 5, "S25+x": 6, "S25-x": 7,
+       "S03+y": 8, "S03-y": 9, "S25+y": 10, "S25-y": 11, "VX": 12, "VY": 13}
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ENOMEM", 3: "QLA_ECUDA", 4: "QLA_ETIMEOUT",
           5: "QLA_ENONFINITE", 6: "QLA_EUNSUPPORTED", 7: "QLA_ESTATE"}
@@ -29,7 +33,7 @@ STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ENOMEM", 3: "QLA_ECUDA", 4: "QLA
 # Every symbol include/qla.h declares (checked by the tests).
 EXPORTS = [
     "qla_default_options", "qla_query_buffer_sizes", "qla_create", "qla_init_pulse", "qla_set_fields",
-    "qla_set_fields_f32", "qla_step", "qla_energy", "qla_divB", "qla_diagnostics", "qla_get_fields",
+    "qla_set_fields_f32", "qla_step", "qla_debug_apply", "qla_energy", "qla_divB", "qla_diagnostics", "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
     "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc",
     "qla_batch_create", "qla_batch_run", "qla_batch_get_fields_f32", "qla_batch_diagnostics", "qla_batch_info",
@@ -91,6 +95,8 @@ def load_library(path: str = LIB_PATH):
     L.qla_set_fields_f32.restype = st
     L.qla_step.argtypes = [v, ctypes.c_longlong]
     L.qla_step.restype = st
+    L.qla_debug_apply.argtypes = [v, i, i]
+    L.qla_debug_apply.restype = st
     L.qla_energy.argtypes = [v, P(d)]
     L.qla_energy.restype = st
     L.qla_divB.argtypes = [v, P(d), P(d), P(d)]
@@ -256,6 +262,10 @@ class Simulation:
 
     def step(self, nsteps: int):
         self._check(self._L.qla_step(self._ctx, int(nsteps)), "qla_step")
+
+    def debug_apply(self, op: str, count: int = 1):
+        """Apply one operator of the step (see OPS) `count` times."""
+        self._check(self._L.qla_debug_apply(self._ctx, _code("op", OPS, op), int(count)), "qla_debug_apply")
 
     def diagnostics(self) -> dict:
         d = Diag()
