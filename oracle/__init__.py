@@ -70,6 +70,7 @@ def lib():
             L.orc_energy.argtypes = [i, i, d]
             L.orc_energy.restype = ctypes.c_double
             L.orc_divB.argtypes = [i, i, d, d]
+            L.orc_divD.argtypes = [i, i, d, d, d, d, d]
             L.orc_init_pulse.argtypes = [i, i, d, i, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_yee_run.argtypes = [i, i, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, d, d, d]
             _lib = L
@@ -157,6 +158,16 @@ def divB(q):
     q = _f64(q)
     out = np.zeros(3)
     lib().orc_divB(q.shape[2], q.shape[1], _p(q), _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def divD(q, n_x, n_y, n_z):
+    """(sum div^2, max |div|, max |D|) of D = (n_x q0, n_y q1, n_z q2) (eps_i = n_i^2)
+    with central differences."""
+    q = _f64(q)
+    nx, ny, nz = _f64(n_x), _f64(n_y), _f64(n_z)
+    out = np.zeros(3)
+    lib().orc_divD(q.shape[2], q.shape[1], _p(q), _p(nx), _p(ny), _p(nz), _p(out))
     return float(out[0]), float(out[1]), float(out[2])
 
 

@@ -412,6 +412,40 @@ void orc_divB(int Nx, int Ny, const double *q, double *out)
 }
 
 /* ---------------------------------------------------------------------------
+ * Divergence of D (Sec. 4.2: with the E_y polarisation the QLA generates an
+ * E_x field so that div D = 0), in lattice units with central differences at
+ * the sites. The dielectric tensor is diagonal with eps_i = n_i^2, so with
+ * q0 = n_x E_x, q1 = n_y E_y, q2 = n_z E_z (Eq. 15):
+ *   D_x = n_x q0,  D_y = n_y q1,  D_z = n_z q2 (no z dependence in 2D),
+ *   div = (D_x[x+1]-D_x[x-1])/2 + (D_y[y+1]-D_y[y-1])/2.
+ * out[0] = sum div^2, out[1] = max |div|, out[2] = max |D|.
+ * ------------------------------------------------------------------------- */
+void orc_divD(int Nx, int Ny, const double *q, const double *nx, const double *ny, const double *nz, double *out)
+{
+    const size_t P = plane_of(Nx, Ny);
+    double s = 0.0, c = 0.0, mdiv = 0.0, md = 0.0;
+    for (int y = 0; y < Ny; ++y) {
+        const int yp = wrap(y + 1, Ny), ym = wrap(y - 1, Ny);
+        for (int x = 0; x < Nx; ++x) {
+            const int xp = wrap(x + 1, Nx), xm = wrap(x - 1, Nx);
+            const size_t i = (size_t)y * Nx + x;
+            const size_t ixp = (size_t)y * Nx + xp, ixm = (size_t)y * Nx + xm;
+            const size_t iyp = (size_t)yp * Nx + x, iym = (size_t)ym * Nx + x;
+            const double d = 0.5 * (nx[ixp] * q[0 * P + ixp] - nx[ixm] * q[0 * P + ixm]) +
+                             0.5 * (ny[iyp] * q[1 * P + iyp] - ny[iym] * q[1 * P + iym]);
+            neumaier_add(&s, &c, d * d);
+            if (fabs(d) > mdiv) mdiv = fabs(d);
+            const double dx = nx[i] * q[0 * P + i], dy = ny[i] * q[1 * P + i], dz = nz[i] * q[2 * P + i];
+            const double dm = sqrt(dx * dx + dy * dy + dz * dz);
+            if (dm > md) md = dm;
+        }
+    }
+    out[0] = s + c;
+    out[1] = mdiv;
+    out[2] = md;
+}
+
+/* ---------------------------------------------------------------------------
  * Initial 1D Gaussian pulse travelling in +x (Sec. 2.2 energy discussion and
  * Sec. 4: a 1D pulse propagating in x). g(x) = amp exp(-d^2/(2 sigma^2)) with
  * d the periodic minimum-image distance x - x0; uniform in y.

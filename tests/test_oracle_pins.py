@@ -214,6 +214,41 @@ def test_divB_closed_form():
     assert abs(b - 1.0) < 1e-14
 
 
+def test_divD_discrete_curl_is_divergence_free_in_an_anisotropic_medium():
+    """D = (n_x q0, n_y q1) built as the discrete curl of a potential has zero
+    central-difference divergence; with n_x != n_y a divergence that weighted a
+    component with the wrong index (or ignored it) would not vanish."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((20, 24))
+    nx = 1.0 + rng.random((20, 24))
+    ny = 2.0 + rng.random((20, 24))
+    nz = 1.5 + rng.random((20, 24))
+    Dx = lambda f: 0.5 * (np.roll(f, -1, axis=1) - np.roll(f, 1, axis=1))
+    Dy = lambda f: 0.5 * (np.roll(f, -1, axis=0) - np.roll(f, 1, axis=0))
+    q = np.zeros((6, 20, 24))
+    q[0] = Dy(A) / nx
+    q[1] = -Dx(A) / ny
+    s, m, _ = oracle.divD(q, nx, ny, nz)
+    assert m < 1e-14 and s < 1e-26
+    s_wrong, _, _ = oracle.divD(q, ny, nx, nz)
+    assert s_wrong > 1e-2
+
+
+def test_divD_closed_form():
+    """D_x = n_x q0 = sin(2 pi x / Nx) in a uniform medium: div = cos(2 pi x / Nx) sin(2 pi / Nx)."""
+    Nx, Ny, n = 32, 6, 1.7
+    x = np.arange(Nx)
+    q = np.zeros((6, Ny, Nx))
+    q[0] = np.sin(2 * math.pi * x / Nx)[None, :] / n
+    q[2] = 0.5 / 2.0
+    ones = np.ones((Ny, Nx))
+    s, m, dmax = oracle.divD(q, n * ones, 1.3 * ones, 2.0 * ones)
+    k = math.sin(2 * math.pi / Nx)
+    assert abs(s - Ny * (Nx / 2) * k * k) < 1e-12
+    assert abs(m - k) < 1e-14
+    assert abs(dmax - math.sqrt(1.0 + 0.25)) < 1e-14  # |D| = sqrt(D_x^2 + D_z^2), D_z = 2.0 * 0.25
+
+
 # ---------------------------------------------------------------------------
 # Pulse initialisation
 # ---------------------------------------------------------------------------
