@@ -158,6 +158,14 @@ qla_status qla_energy(qla_ctx *ctx, double *energy);
  * *max_absB = max |B|. FP64, deterministic. Synchronises. */
 qla_status qla_divB(qla_ctx *ctx, double *l2_sq_sum, double *max_abs, double *max_absB);
 
+/* Divergence of D (Sec. 4.2: for the E_y polarisation the QLA generates E_x so
+ * that div D = 0). The dielectric tensor is diagonal with eps_i = n_i^2, so
+ * D = (n_x q0, n_y q1, n_z q2) (Eq. 15); div D = (D_x[x+1] - D_x[x-1])/2 +
+ * (D_y[y+1] - D_y[y-1])/2 in lattice units at the sites, periodic. Outputs:
+ * sum over sites of div^2, max |div|, max |D|; FP64 with compensated sums,
+ * deterministic. Synchronous. QLA_ENONFINITE if q0, q1 or q2 holds NaN/Inf. */
+qla_status qla_divD(qla_ctx *ctx, double *l2_sq_sum, double *max_abs, double *max_absD);
+
 /* All diagnostics from one reduction pass. nonfinite = number of non-finite
  * state values; when it is non-zero the call returns QLA_ENONFINITE (not
  * sticky) with the other fields still filled in. */

@@ -444,6 +444,23 @@ qla_status qla_divB(qla_ctx *c, double *l2_sq_sum, double *max_abs, double *max_
     return s;
 }
 
+qla_status qla_divD(qla_ctx *c, double *l2_sq_sum, double *max_abs, double *max_absD) {
+    qla_status s = enter(c);
+    if (s != QLA_OK) return s;
+    if (!c->has_state) return fail(c, QLA_ESTATE, "no state set (call qla_init_pulse or qla_set_fields)");
+    cudaError_t e = qla::launch_divD(c->state[c->cur], c->opt.precision == QLA_FP64 ? 1 : 0, c->index, c->Nx, c->Ny,
+                                     c->scratch, c->diag_dev, c->stream);
+    if (e != cudaSuccess) return fail(c, QLA_ECUDA, "div D launch: %s", cudaGetErrorString(e));
+    QLA_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_dev, sizeof(qla::DiagResult), cudaMemcpyDeviceToHost,
+                                c->stream));
+    s = check_sweep_error(c);
+    if (s != QLA_OK) return s;
+    if (l2_sq_sum) *l2_sq_sum = c->diag_host->div_sq_sum;
+    if (max_abs) *max_abs = c->diag_host->div_max;
+    if (max_absD) *max_absD = c->diag_host->b_max;
+    return c->diag_host->nonfinite ? QLA_ENONFINITE : QLA_OK;
+}
+
 qla_status qla_get_fields(qla_ctx *c, double *q) {
     qla_status s = enter(c);
     if (s != QLA_OK) return s;

@@ -42,6 +42,32 @@ __device__ __forceinline__ bool finite_val(T v) {
     return isfinite(v);
 }
 
+__device__ __forceinline__ void merge_into(Partial &a, const Partial &b) {
+    CSum es{a.e_s, a.e_c}, ds{a.d_s, a.d_c};
+    es.merge(CSum{b.e_s, b.e_c});
+    ds.merge(CSum{b.d_s, b.d_c});
+    a.e_s = es.s; a.e_c = es.c; a.d_s = ds.s; a.d_c = ds.c;
+    a.dmax = fmax(a.dmax, b.dmax);
+    a.bmax = fmax(a.bmax, b.bmax);
+    a.nonfinite += b.nonfinite;
+}
+
+// The block's threads combined in a fixed tree; thread 0 writes the record.
+__device__ __forceinline__ void block_reduce_write(const Partial &mine, Partial *__restrict__ part) {
+    __shared__ Partial sh[DIAG_THREADS];
+    sh[threadIdx.x] = mine;
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            Partial a = sh[threadIdx.x];
+            merge_into(a, sh[threadIdx.x + w]);
+            sh[threadIdx.x] = a;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_partial(const T *__restrict__ q, int Nx, int Ny,
                                                              Partial *__restrict__ part) {
@@ -81,25 +107,42 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial(const T *__restrict
         d.add(drow);
     }
     const double bmax = sqrt(b2max);  // sqrt is monotonic: the max of the site norms
-    __shared__ Partial sh[DIAG_THREADS];
-    sh[threadIdx.x] = Partial{e.s, e.c, d.s, d.c, dmax, bmax, nf, 0ull};
-    __syncthreads();
-    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            Partial a = sh[threadIdx.x];
-            const Partial b = sh[threadIdx.x + w];
-            CSum es{a.e_s, a.e_c}, ds{a.d_s, a.d_c};
-            es.merge(CSum{b.e_s, b.e_c});
-            ds.merge(CSum{b.d_s, b.d_c});
-            a.e_s = es.s; a.e_c = es.c; a.d_s = ds.s; a.d_c = ds.c;
-            a.dmax = fmax(a.dmax, b.dmax);
-            a.bmax = fmax(a.bmax, b.bmax);
-            a.nonfinite += b.nonfinite;
-            sh[threadIdx.x] = a;
+    block_reduce_write(Partial{e.s, e.c, d.s, d.c, dmax, bmax, nf, 0ull}, part);
+}
+
+// Divergence of D (Sec. 4.2): D = (n_x q0, n_y q1, n_z q2) for the diagonal
+// dielectric eps_i = n_i^2 (Eq. 15: q_i = n_i E_i), central differences in
+// lattice units; the same partition and trees as diag_partial. The record's
+// div fields hold sum div^2 and max |div|, its B field max |D|; the energy
+// fields are zero.
+template <typename T>
+__global__ void __launch_bounds__(DIAG_THREADS) divD_partial(const T *__restrict__ q, const double *__restrict__ idx,
+                                                             int Nx, int Ny, Partial *__restrict__ part) {
+    const size_t P = size_t(Nx) * size_t(Ny);
+    const T *q0 = q, *q1 = q + P, *q2 = q + 2 * P;
+    const double *nx = idx, *ny = idx + P, *nz = idx + 2 * P;
+    CSum d{0.0, 0.0};
+    double dmax = 0.0, d2max = 0.0;
+    unsigned long long nf = 0;
+    for (int y = blockIdx.x; y < Ny; y += gridDim.x) {
+        const int yp = y + 1 == Ny ? 0 : y + 1, ym = y == 0 ? Ny - 1 : y - 1;
+        const size_t r = size_t(y) * Nx;
+        double drow = 0.0;
+        for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
+            const size_t i = r + x;
+            const int xp = x + 1 == Nx ? 0 : x + 1, xm = x == 0 ? Nx - 1 : x - 1;
+            const size_t ixp = r + xp, ixm = r + xm, iyp = size_t(yp) * Nx + x, iym = size_t(ym) * Nx + x;
+            const double dv = 0.5 * (nx[ixp] * double(q0[ixp]) - nx[ixm] * double(q0[ixm])) +
+                              0.5 * (ny[iyp] * double(q1[iyp]) - ny[iym] * double(q1[iym]));
+            drow = fma(dv, dv, drow);
+            dmax = fmax(dmax, fabs(dv));
+            const double dx = nx[i] * double(q0[i]), dy = ny[i] * double(q1[i]), dz = nz[i] * double(q2[i]);
+            d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
+            if (!finite_val(q0[i]) || !finite_val(q1[i]) || !finite_val(q2[i])) ++nf;
         }
-        __syncthreads();
+        d.add(drow);
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+    block_reduce_write(Partial{0.0, 0.0, d.s, d.c, dmax, sqrt(d2max), nf, 0ull}, part);
 }
 
 __global__ void __launch_bounds__(DIAG_THREADS) diag_final(const Partial *__restrict__ part, int n,
@@ -162,6 +205,20 @@ cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, voi
         diag_partial<float><<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, part);
     else
         diag_partial<double><<<G, DIAG_THREADS, 0, st>>>(static_cast<const double *>(q), Nx, Ny, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final<<<1, DIAG_THREADS, 0, st>>>(part, G, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divD(const void *q, int precision, const double *index, int Nx, int Ny, void *scratch,
+                        DiagResult *out_dev, cudaStream_t st) {
+    const int G = diag_blocks(Nx, Ny);
+    Partial *part = static_cast<Partial *>(scratch);
+    if (precision == 0)
+        divD_partial<float><<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), index, Nx, Ny, part);
+    else
+        divD_partial<double><<<G, DIAG_THREADS, 0, st>>>(static_cast<const double *>(q), index, Nx, Ny, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final<<<1, DIAG_THREADS, 0, st>>>(part, G, out_dev);

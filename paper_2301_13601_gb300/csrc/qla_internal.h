@@ -85,6 +85,10 @@ int diag_blocks(int Nx, int Ny);
 size_t diag_scratch_bytes(int Nx, int Ny);
 cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, void *scratch,
                                DiagResult *out_dev, cudaStream_t st);
+// div D statistics in the DiagResult fields div_sq_sum, div_max and b_max
+// (= max |D|); index: the FP64 fields n_x, n_y, n_z [3][Ny][Nx].
+cudaError_t launch_divD(const void *q, int precision, const double *index, int Nx, int Ny, void *scratch,
+                        DiagResult *out_dev, cudaStream_t st);
 
 
 // ---------------------------------------------------------------------------

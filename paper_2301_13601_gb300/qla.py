@@ -33,7 +33,8 @@ STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ENOMEM", 3: "QLA_ECUDA", 4: "QLA
 # Every symbol include/qla.h declares (checked by the tests).
 EXPORTS = [
     "qla_default_options", "qla_query_buffer_sizes", "qla_create", "qla_init_pulse", "qla_set_fields",
-    "qla_set_fields_f32", "qla_step", "qla_debug_apply", "qla_energy", "qla_divB", "qla_diagnostics", "qla_get_fields",
+    "qla_set_fields_f32", "qla_step", "qla_debug_apply", "qla_energy", "qla_divB", "qla_divD", "qla_diagnostics",
+    "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
     "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc",
     "qla_batch_create", "qla_batch_run", "qla_batch_get_fields_f32", "qla_batch_diagnostics", "qla_batch_info",
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     L.qla_energy.restype = st
     L.qla_divB.argtypes = [v, P(d), P(d), P(d)]
     L.qla_divB.restype = st
+    L.qla_divD.argtypes = [v, P(d), P(d), P(d)]
+    L.qla_divD.restype = st
     L.qla_diagnostics.argtypes = [v, P(Diag)]
     L.qla_diagnostics.restype = st
     L.qla_get_fields.argtypes = [v, P(d)]
@@ -287,6 +290,14 @@ class Simulation:
         st = self._L.qla_divB(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
         if st not in (0, 5):
             self._check(st, "qla_divB")
+        return a.value, b.value, c.value
+
+    def divD(self):
+        """(sum div^2, max |div|, max |D|) of D = (n_x q0, n_y q1, n_z q2)."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = self._L.qla_divD(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        if st not in (0, 5):
+            self._check(st, "qla_divD")
         return a.value, b.value, c.value
 
     def synchronize(self):
