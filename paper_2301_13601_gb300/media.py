@@ -82,6 +82,19 @@ def medium(Nx: int, Ny: int, objects: Sequence[Ellipse]) -> Tuple[np.ndarray, np
     return np.ascontiguousarray(n[0]), np.ascontiguousarray(n[1]), np.ascontiguousarray(n[2])
 
 
+def cone_cylinder_medium(N: int, r_cone: float, r_cyl: float, n_max: float = 3.0, w: float = 8.0):
+    """The anisotropic object of the paper's scattering runs (Sec. 4, Fig. 2),
+    centred on an N x N lattice in vacuum: n_z conical (n_max at the centre,
+    falling linearly to 1 at radius r_cone), n_x = n_y cylindrical (n_max
+    inside radius r_cyl, a tanh edge of width w). The radii are not given in
+    the paper; callers choose and record them."""
+    y, x = np.meshgrid(np.arange(N, dtype=np.float64), np.arange(N, dtype=np.float64), indexing="ij")
+    r = np.hypot(x - N / 2, y - N / 2)
+    n_z = 1.0 + (n_max - 1.0) * np.clip(1.0 - r / r_cone, 0.0, None)
+    n_xy = 1.0 + (n_max - 1.0) * 0.5 * (1.0 - np.tanh((r - r_cyl) / w))
+    return np.ascontiguousarray(n_xy), np.ascontiguousarray(n_xy.copy()), np.ascontiguousarray(n_z)
+
+
 def uniform_medium(Nx: int, Ny: int, n: Tuple[float, float, float]):
     return tuple(np.full((Ny, Nx), float(v)) for v in n)
 
