@@ -361,6 +361,8 @@ def single_family_report(w, args, peak, peak_kind, steps: int = 5):
 
 
 SURROGATE_CHECKPOINT = os.path.join(ROOT, "paper_2301_13601_gb300", "checkpoints", "surrogate_k16.npz")
+# the same network advancing 32 steps per call (trained from the 16-step weights)
+SURROGATE_CHECKPOINT_K32 = os.path.join(ROOT, "paper_2301_13601_gb300", "checkpoints", "surrogate_k32.npz")
 
 
 def surrogate_report(calls: int = 250, seed: int = 7):
@@ -392,6 +394,20 @@ def surrogate_report(calls: int = 250, seed: int = 7):
     bf16 = peaks.get("bf16_tflops") or 1900.0
     achieved = flops / r["forward_seconds_per_call"] / 1e12
     curve = [(c["steps"], round(c["rel_l2"], 5)) for c in r["curve"][4::5]]
+    variants = []
+    if os.path.exists(SURROGATE_CHECKPOINT_K32):
+        p32, m32 = T.load_checkpoint(SURROGATE_CHECKPOINT_K32)
+        calls32 = calls * meta["K"] // m32["K"]
+        with S.Surrogate(w.Ny, w.Nx, nimg=1, K=m32["K"], out_scale=m32["out_scale"]) as sur:
+            sur.set_params(p32)
+            r32 = T.evaluate(sur, w, calls32, drift_tol=1e-3, checkpoints=calls32 // 5)
+        variants.append({
+            "K": m32["K"], "checkpoint": os.path.relpath(SURROGATE_CHECKPOINT_K32, ROOT),
+            "trained": {k: m32[k] for k in ("trajectories", "iters", "noise", "final_loss", "train_seconds")},
+            "rel_l2": r32["rel_l2"], "horizon_steps_rel_l2_1e-2": r32["horizon_steps_rel_l2_1e-2"],
+            "speedup_at_rel_l2_1e-2": r32["speedup_at_rel_l2_1e-2"], "speedup_rollout": r32["speedup_rollout"],
+            "speedup_forward": r32["speedup_forward"], "surrogate_calls": r32["surrogate_calls"],
+            "fallback_calls": r32["fallback_calls"]})
     return {
         "workload": f"surrogate1024 seed {seed}: 1024x1024, delta 0.05, {calls} calls x 16 steps",
         "checkpoint": os.path.relpath(SURROGATE_CHECKPOINT, ROOT),
@@ -407,6 +423,9 @@ def surrogate_report(calls: int = 250, seed: int = 7):
         "qla_ms_per_16_steps": 1e3 * r["qla_seconds_per_K"],
         "forward_ms_per_call": 1e3 * r["forward_seconds_per_call"],
         "rel_l2_curve": curve,
+        # steps per call at which one forward costs as much as plain QLA for those steps
+        "break_even_K": meta["K"] * r["forward_seconds_per_call"] / r["qla_seconds_per_K"],
+        "variants": variants,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                      "frac": achieved / bf16, "peak_kind": "measured" if peaks.get("bf16_tflops") else "fallback",
                      "kernel": "conv3x3_tc_kernel (6 layers, one forward call)",

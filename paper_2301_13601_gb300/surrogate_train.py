@@ -238,20 +238,24 @@ def main(argv=None):
     ap.add_argument("--noise", type=float, default=0.0)
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--init", default=None, help="start from this checkpoint")
+    ap.add_argument("--K", type=int, default=16, help="QLA steps per surrogate call")
     a = ap.parse_args(argv)
-    K = 16
+    K = a.K
+    # output scale K/256 (1/16 at K = 16): a checkpoint trained for K steps,
+    # loaded for 2K steps, starts from twice its per-call update
+    out_scale = K / 256.0
     rng = np.random.default_rng(a.seed)
     t0 = time.perf_counter()
     wl = [training_workload(rng, a.nx, a.ny, 0.05, a.steps) for _ in range(a.trajectories)]
     data = generate(wl, K)
     t1 = time.perf_counter()
-    with Surrogate(a.ny, a.nx, nimg=a.batch, K=K, train=True, seed=a.seed) as sur:
+    with Surrogate(a.ny, a.nx, nimg=a.batch, K=K, out_scale=out_scale, train=True, seed=a.seed) as sur:
         if a.init:
             sur.set_params(load_checkpoint(a.init)[0])
         hist = train(sur, data, a.iters, lr=a.lr, log_every=max(1, a.iters // 40), seed=a.seed, noise=a.noise)
         params = sur.get_params()
     t2 = time.perf_counter()
-    meta = {"K": K, "out_scale": 1.0 / 16, "trajectories": a.trajectories, "steps": a.steps, "lattice": [a.nx, a.ny],
+    meta = {"K": K, "out_scale": out_scale, "trajectories": a.trajectories, "steps": a.steps, "lattice": [a.nx, a.ny],
             "delta": 0.05, "iters": a.iters, "batch": a.batch, "lr": a.lr, "noise": a.noise, "seed": a.seed,
             "init": a.init, "final_loss": hist[-1][1], "data_seconds": t1 - t0, "train_seconds": t2 - t1,
             "gpu": torch.cuda.get_device_name()}

@@ -7,6 +7,8 @@ forward chain holds about 10 such roundings (z and a of five layers) and the
 backward about as many again (g, dz), so the derived tolerance is
 sqrt(20) x 2^-9 x 3 (an amplification margin) ~ 3e-2 on relative L2 errors.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -195,6 +197,23 @@ def test_trained_checkpoint_gains_over_the_method_without_it():
     assert tr["rel_l2"] < 0.05 * tr["rel_l2_no_update"]
     assert tr["rel_l2"] < 0.05 * un["rel_l2"]
     assert tr["rel_l2"] < 1e-2  # 512 steps within the error bound
+
+
+def test_k32_checkpoint_within_the_error_bound_on_a_held_out_lattice():
+    """The 32-steps-per-call checkpoint (trained from the 16-step weights):
+    512 steps on a held-out lattice within rel L2 1e-2, far below no update."""
+    from paper_2301_13601_gb300 import surrogate_train as T
+
+    path = os.path.join(os.path.dirname(T.DEFAULT_CHECKPOINT), "surrogate_k32.npz")
+    params, meta = T.load_checkpoint(path)
+    assert meta["K"] == 32
+    w = T.training_workload(np.random.default_rng(999), 512, 256, 0.05, 512)
+    with S.Surrogate(256, 512, K=32, out_scale=meta["out_scale"]) as sur:
+        sur.set_params(params)
+        tr = T.evaluate(sur, w, 16, drift_tol=1e30, checkpoints=4)
+    print("K32 trained", tr["rel_l2"], "no update", tr["rel_l2_no_update"])
+    assert tr["fallback_calls"] == 0 and tr["surrogate_calls"] == 16
+    assert tr["rel_l2"] < 1e-2 and tr["rel_l2"] < 0.05 * tr["rel_l2_no_update"]
 
 
 def test_short_training_from_scratch_improves_held_out_error():
