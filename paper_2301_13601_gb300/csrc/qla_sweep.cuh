@@ -70,6 +70,7 @@ struct SweepParams {
     CUtensorMap tm_coef_m;
     int tma;
     int merged;
+    int tiles_fastest;  // grid x runs over the row tiles of a strip (else over the strips of a tile row)
 };
 
 template <typename T>
@@ -745,11 +746,13 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const CUtensorMap *ts = prm.tma ? &prm.tm_state : nullptr;
     const CUtensorMap *tcf = prm.tma ? &prm.tm_coef : nullptr;
+    const int strip = prm.tiles_fastest ? blockIdx.y : blockIdx.x;
+    const int chunk = prm.tiles_fastest ? blockIdx.x : blockIdx.y;
     if (prm.a.fam0 + int(blockIdx.z) == 0)
-        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf, &prm.tm_state_r,
+        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, strip, chunk, smem_raw, ts, tcf, &prm.tm_state_r,
                                                 &prm.tm_coef_r, prm.merged ? &prm.tm_coef_m : nullptr);
     else
-        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, blockIdx.x, blockIdx.y, smem_raw, ts, tcf, &prm.tm_state_r,
+        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, strip, chunk, smem_raw, ts, tcf, &prm.tm_state_r,
                                                 &prm.tm_coef_r, prm.merged ? &prm.tm_coef_m : nullptr);
 }
 
@@ -850,7 +853,14 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, K, R, prm)) ? 1 : 0;
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
-    dim3 grid(nsx, ncy, nfam);
+    // CTA order. One 224 KB CTA per SM (K = 4): the tiles of a strip in a row,
+    // so that a tile's warm-up rows were just read by its neighbour above
+    // (8192^2: 58.6 vs 55.0 G site-updates/s). Two CTAs per SM: the strips of
+    // a tile row in a row (equal or better there). Families stay in separate
+    // halves of the grid: two resident CTAs of different families (different
+    // code) ran 13% slower.
+    prm.tiles_fastest = K >= 4 ? 1 : 0;
+    const dim3 grid = prm.tiles_fastest ? dim3(ncy, nsx, nfam) : dim3(nsx, ncy, nfam);
     sweep_kernel<T, K, R, NY, INTER, UNIT><<<grid, Cfg::NT, L::SMEM, st>>>(prm);
     return cudaGetLastError();
 }
