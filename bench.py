@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 # DRAM bytes per sweep launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
 # excluded), the workload, steps per pass and rows per tile match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "1017c91b72cebb6b", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 2, "chunk_rows": 216, "bytes_per_launch": 6.140e9 + 1.593e9}
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "59088c96c7c8ea6b", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 2, "chunk_rows": 216, "bytes_per_launch": 6.142e9 + 1.593e9}
 
 L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"
