@@ -275,8 +275,11 @@ cudaError_t dalloc(qla_batch *b, P **p, size_t bytes) {
     return e;
 }
 
+// Rows per tile in the batch. Measured on the 64-lattice workload (sides
+// 256-2048, 4 steps per pass), site-updates/s: 512 rows 52.5 G, 768 and 1024
+// rows 53.3 G, 2048 rows 50.1 G.
 int auto_batch_chunk(int Ny) {
-    int ch = std::min(Ny, 512);
+    int ch = std::min(Ny, 768);
     return std::max(1, ch);
 }
 
