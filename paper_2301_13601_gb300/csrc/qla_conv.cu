@@ -3,13 +3,15 @@
 //
 // Activations hold nimg images of H x W stacked ([nimg][H][W][C]); each image
 // is periodic on its own. One tile = 128 consecutive pixels of one image row
-// (M = 128), all output
-// channels (N = NOUT), K = 9 taps x input channels. The CTA stages the 3-row
-// halo block (3 x 130 pixels x CIN channels) once per tile in the interleaved
-// K-major layout, so the nine taps are nine shifted windows of the same block
-// (no swizzle: any 16-byte aligned start is a valid operand). All 9 taps of the
+// (M = 128), all output channels, K = 9 taps x input channels. Input rows
+// (130 pixels with the x halo, CIN channels) are staged once each in the
+// interleaved K-major layout, so the three x taps are shifted windows of the
+// same row (no swizzle: any 16-byte aligned start is a valid operand). Each
+// staged input row is multiplied once per (x tap, 16-channel slice) against
+// the weights of all three y taps at once (N = 3 NOUT), accumulating into the
+// TMEM accumulators of the three output rows it feeds. All 9 taps of the
 // packed weights stay resident in shared memory. One thread issues the MMAs;
-// the 128 threads (4 warps x 32 TMEM lanes) run the fused epilogue:
+// the epilogue warps (32 TMEM lanes each) run the fused epilogue:
 //   EPI_GELU      z = acc + b;  act = GELU(z) (+ residual);  stores act and, if asked, z (BF16)
 //   EPI_LINEAR    out = acc + b (FP32, NOUT channels)
 //   EPI_DGRAD     g = acc + g_in (FP32);  dz = BF16(g * GELU'(z_prev))
@@ -63,19 +65,23 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
 }
 
 // Shared memory: a ring of NS halo rows, As[c][slot][130 px][16 B] (c = 8-channel
-// chunk), then the packed weights of all nine taps, Bs[t][c][n][16 B].
+// chunk), then the packed weights of all nine taps, Bs[kx][c][ky][n][16 B]
+// (the three y taps consecutive along N).
 template <int CCH, int NOUT>
 struct ConvLayout {
     static constexpr int HALO_PX = 130;
-    static constexpr int NS = CCH >= 8 ? 6 : 8;  // MMA needs 3 rows; the loader runs up to NS-3 rows ahead
+    // Ring depth; even, so that a slot is always released by the same epilogue group.
+    static constexpr int NS = CCH >= 8 && NOUT >= 64 ? 8 : (CCH >= 8 ? 6 : 8);
+    static_assert(NS % 2 == 0, "ring slots alternate between the two epilogue groups");
     static constexpr int A_BYTES = CCH * NS * HALO_PX * 16;
     static constexpr int B_BYTES = 9 * CCH * NOUT * 16;
     static constexpr int A_OFF = 0;
     static constexpr int B_OFF = ((A_BYTES + 1023) / 1024) * 1024;
     static constexpr int SMEM = B_OFF + B_BYTES;
-    static constexpr int ACC_COLS = NOUT < 32 ? 32 : NOUT;  // TMEM columns of one accumulator
-    static constexpr int NACC = 4;                          // accumulators in TMEM
-    static constexpr int TMEM_COLS = NACC * ACC_COLS;
+    // At least half of an SM's shared memory, so one CTA per SM owns all of TMEM.
+    static constexpr int SMEM_LAUNCH = SMEM > 116 * 1024 ? SMEM : 116 * 1024;
+    static constexpr int TMEM_COLS = 512;
+    static constexpr int NB = TMEM_COLS / NOUT;  // output-row accumulators (NOUT columns each)
 };
 
 constexpr int CONV_EPI_WARPS = 8;
@@ -114,19 +120,23 @@ __device__ __forceinline__ ConvSeg conv_segment(long long u0, long long u_end, i
 // halo rows in shared memory, so every input row is loaded once per block.
 //   warp 9 (loader)   cp.async of each halo row into the ring; arrival on
 //                     full[slot] when its copies land; waits on empty[slot]
-//   warp 8 (MMA)      one lane issues the 9 x CCH/2 MMAs of an output row into
-//                     one of two TMEM accumulators, then commits acc_full and
-//                     releases the rows it read last (empty[slot])
+//   warp 8 (MMA)      per input row, one lane issues the 3 x CCH/2 MMAs (x tap,
+//                     16-channel slice) whose N = 3 NOUT columns are the
+//                     accumulators of the three output rows the row feeds,
+//                     then releases the row (empty[slot]) and commits acc_full
+//                     of the output row it completes
 //   warps 0-7 (epilogue) wait acc_full, tcgen05.ld, fused epilogue, stores;
 //                     arrive on acc_empty, and on empty[slot] of the centre
 //                     row (a residual equal to the input is read from the
-//                     ring), so a row is free after its last MMA and its
+//                     ring), so a row is free after its MMAs and its
 //                     epilogue (edge rows of a run get their arrival at the
 //                     run's start and end)
-// Warp w of the epilogue reads TMEM lanes 32 (w % 4).. (its pixels) and the
-// column half w / 4; for NOUT = 16 only warps 0-3 work. Every wait is bounded;
-// a timeout sets the error flag and the role stops, and the others time out
-// in turn, so the kernel always ends.
+// TMEM holds NB = 512 / NOUT accumulators in a ring; output row o (counted
+// over the CTA's runs) owns block (-o) mod NB, so the rows j, j-1, j-2 that
+// input row j feeds are consecutive blocks and one MMA covers them (split in
+// two where the ring wraps). Every wait is bounded; a timeout sets the error
+// flag and the role stops, and the others time out in turn, so the kernel
+// always ends.
 template <int CCH, int NOUT>
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvArgs a) {
     using L = ConvLayout<CCH, NOUT>;
@@ -134,7 +144,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
     constexpr int NS = L::NS;
     constexpr int HP = L::HALO_PX;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full_bar[NS], empty_bar[NS], accf_bar[L::NACC], acce_bar[L::NACC], done_bar;
+    constexpr int NB = L::NB;
+    __shared__ uint64_t full_bar[NS], empty_bar[NS], accf_bar[NB], acce_bar[NB], done_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ float bias_s[64];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -148,7 +159,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
 
     {
         const uint4 *src = static_cast<const uint4 *>(a.w);
-        for (int i = tid; i < 9 * CCH * NOUT; i += CONV_THREADS) cp_async16(Bs + i * 16, src + i);
+        for (int i = tid; i < 9 * CCH * NOUT; i += CONV_THREADS) {  // [t][c][n] -> [kx][c][ky][n]
+            const int n = i % NOUT, c = (i / NOUT) % CCH, t = i / (NOUT * CCH);
+            const int ky = t / 3, kx = t - 3 * ky;
+            cp_async16(Bs + (((kx * CCH + c) * 3 + ky) * NOUT + n) * 16, src + i);
+        }
         cp_async_commit();
         if (tid < 64) bias_s[tid] = (a.bias && tid < NOUT && a.epi != EPI_DGRAD) ? a.bias[tid] : 0.0f;
     }
@@ -158,7 +173,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
             tc::mbar_init(&full_bar[s], 32);
             tc::mbar_init(&empty_bar[s], 1 + CONV_EPI_WARPS / 2);
         }
-        for (int b = 0; b < L::NACC; ++b) {
+        for (int b = 0; b < NB; ++b) {
             tc::mbar_init(&accf_bar[b], 1);
             tc::mbar_init(&acce_bar[b], CONV_EPI_WARPS / 2);
         }
@@ -203,9 +218,16 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
         if (!ok && lane == 0) atomicExch(a.error, 1);
     } else if (warp == CONV_MMA_WARP) {
         // ---------------- MMA issuer ----------------
-        constexpr uint32_t IDESC = tc::make_idesc_bf16(128, NOUT);
+        // Input row j of a run feeds output rows j - ky (ky = 0..2) through
+        // the weights of y tap ky; those rows' accumulators are the blocks
+        // b0, b0 + 1, b0 + 2 (mod NB), b0 = block of output row j. The first
+        // MMA of a new accumulator (x tap 0, first slice, ky = 0) runs alone
+        // with accumulation off; the rest add to what is there.
+        constexpr uint32_t IDESC1 = tc::make_idesc_bf16(128, NOUT);
+        constexpr uint32_t IDESC2 = tc::make_idesc_bf16(128, 2 * NOUT);
+        constexpr uint32_t IDESC3 = tc::make_idesc_bf16(128, 3 * NOUT);
         constexpr uint32_t A_LBO = NS * HP * 16, A_SBO = 128;
-        constexpr uint32_t B_LBO = NOUT * 16, B_SBO = 128;
+        constexpr uint32_t B_LBO = 3 * NOUT * 16, B_SBO = 128;
         const uint64_t ad0 = tc::make_desc(tc::smem_addr(As), A_LBO, A_SBO);
         const uint64_t bd0 = tc::make_desc(tc::smem_addr(Bs), B_LBO, B_SBO);
         const uint32_t a_lo0 = uint32_t(ad0), a_hi = uint32_t(ad0 >> 32);
@@ -214,44 +236,48 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
         bool ok = true;
         for (long long u0 = u_begin; u0 < u_end && ok;) {
             const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
-            for (int i = 0; i < sg.len && ok; ++i, ++o) {
-                // rows g+i .. g+i+2 loaded (the first two were waited for by earlier rows)
-                for (int j = (i == 0 ? 0 : 2); j < 3; ++j) {
-                    const long long r = g + i + j;
-                    if (!tc::mbar_wait(&full_bar[r % NS], uint32_t((r / NS) & 1), CONV_WAIT_TRIES)) ok = false;
-                }
-                const int b = int(o & 3);
-                if (o >= 4 && !tc::mbar_wait(&acce_bar[b], uint32_t(((o >> 2) + 1) & 1), CONV_WAIT_TRIES)) ok = false;
+            for (int j = 0; j < sg.len + 2 && ok; ++j) {
+                const long long r = g + j;   // ring row
+                const long long on = o + j;  // output row whose y tap 0 is this row
+                const int b0 = int((NB - on % NB) % NB);
+                if (!tc::mbar_wait(&full_bar[r % NS], uint32_t((r / NS) & 1), CONV_WAIT_TRIES)) ok = false;
+                // a new accumulator reuses the block of output row on - NB
+                if (ok && j < sg.len && on >= NB &&
+                    !tc::mbar_wait(&acce_bar[b0], uint32_t(((on / NB) + 1) & 1), CONV_WAIT_TRIES))
+                    ok = false;
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (lane == 0) {
-                    const uint32_t d = tmem + b * L::ACC_COLS;
-                    uint32_t accum = 0;
+                    const int k_lo = j - sg.len + 1 > 0 ? j - sg.len + 1 : 0;  // y taps whose output row
+                    const int k_hi = j < 2 ? j : 2;                          // lies inside the run
+                    const int wrap = NB - b0;  // first ky whose block wraps to 0
+                    const uint32_t a_row = a_lo0 + uint32_t(int(r % NS) * HP);  // (slot * HP * 16) >> 4
 #pragma unroll
-                    for (int ky = 0; ky < 3; ++ky) {
-                        const int slot = int((g + i + ky) % NS);
-                        const uint32_t a_row = a_lo0 + uint32_t(slot * HP);  // (slot * HP * 16) >> 4
+                    for (int kx = 0; kx < 3; ++kx) {
 #pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) {
-                            const int t = ky * 3 + kx;
-#pragma unroll
-                            for (int k2 = 0; k2 < CCH / 2; ++k2) {
-                                tc::mma_bf16_lohi(d, a_row + uint32_t((2 * k2) * NS * HP + kx), a_hi,
-                                                  b_lo0 + uint32_t((t * CCH + 2 * k2) * NOUT), b_hi, IDESC, accum);
-                                accum = 1;
+                        for (int k2 = 0; k2 < CCH / 2; ++k2) {
+                            const bool first = kx == 0 && k2 == 0;
+                            const uint32_t a_lo = a_row + uint32_t((2 * k2) * NS * HP + kx);
+                            const uint32_t b_lo = b_lo0 + uint32_t((kx * CCH + 2 * k2) * 3 * NOUT);
+                            for (int ka = k_lo; ka <= k_hi;) {
+                                int kb = k_hi;
+                                if (ka < wrap && wrap <= kb) kb = wrap - 1;
+                                if (first && ka == 0) kb = 0;
+                                const int blk = b0 + ka < NB ? b0 + ka : b0 + ka - NB;
+                                const uint32_t idesc = kb == ka ? IDESC1 : (kb == ka + 1 ? IDESC2 : IDESC3);
+                                tc::mma_bf16_lohi(tmem + uint32_t(blk * NOUT), a_lo, a_hi, b_lo + uint32_t(ka * NOUT),
+                                                  b_hi, idesc, (first && ka == 0) ? 0u : 1u);
+                                ka = kb + 1;
                             }
                         }
                     }
-                    tc::mma_commit(&accf_bar[b]);
-                    tc::mma_commit(&empty_bar[(g + i) % NS]);  // row g+i is not read again
-                    if (i == sg.len - 1) {
-                        tc::mma_commit(&empty_bar[(g + i + 1) % NS]);
-                        tc::mma_commit(&empty_bar[(g + i + 2) % NS]);
-                    }
+                    tc::mma_commit(&empty_bar[r % NS]);  // the tensor cores are done with row r
+                    if (j >= 2) tc::mma_commit(&accf_bar[int((NB - (on - 2) % NB) % NB)]);  // output row on - 2
                 }
                 __syncwarp();
             }
             g += sg.len + 2;
+            o += sg.len;
             u0 += sg.len;
         }
         if (lane == 0) {
@@ -282,8 +308,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
             if (lane == 0 && int((o_seg - 1) & 1) == grp) mbar_arrive(&empty_bar[g % NS]);  // first halo row
             for (int i = 0; i < sg.len; ++i, ++o) {
                 if (int(o & 1) != grp) continue;
-                const int b = int(o & 3);
-                if (!tc::mbar_wait(&accf_bar[b], uint32_t((o >> 2) & 1), CONV_WAIT_TRIES)) {
+                const int b = int((NB - o % NB) % NB);
+                if (!tc::mbar_wait(&accf_bar[b], uint32_t((o / NB) & 1), CONV_WAIT_TRIES)) {
                     ok = false;
                     break;
                 }
@@ -294,7 +320,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
                     const int y = sg.y_s + i;
                     const size_t p = ((size_t)sg.img * H + y) * W + sg.x0 + m;
                     float v[32];
-                    tc::tmem_ld32(tmem + b * L::ACC_COLS + cb0 + (uint32_t(32 * q) << 16), v);
+                    const uint32_t ta = tmem + uint32_t(b * NOUT + cb0) + (uint32_t(32 * q) << 16);
+                    if constexpr (NC == 32) tc::tmem_ld32(ta, v);
+                    else tc::tmem_ld16(ta, v);
 #pragma unroll
                     for (int k = 0; k < NC; ++k) v[k] += bias_s[cb0 + k];
                     if (a.epi == EPI_GELU) {
@@ -401,14 +429,14 @@ template <int CCH, int NOUT>
 cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st) {
     using L = ConvLayout<CCH, NOUT>;
     cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CCH, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         L::SMEM);
+                                         L::SMEM_LAUNCH);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long rows = (long long)a.nimg * a.H * (a.W / 128);
     const int grid = rows < sms ? int(rows) : sms;
-    conv3x3_tc_kernel<CCH, NOUT><<<grid, CONV_THREADS, L::SMEM, st>>>(a);
+    conv3x3_tc_kernel<CCH, NOUT><<<grid, CONV_THREADS, L::SMEM_LAUNCH, st>>>(a);
     return cudaGetLastError();
 }
 

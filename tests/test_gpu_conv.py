@@ -79,6 +79,38 @@ def test_conv_gelu_epilogue(residual):
     assert np.max(np.abs(ag - act)) < 2 ** -8 * (np.abs(act).max() + 1.0) * 1.5
 
 
+# Long runs of rows per CTA (152 CTAs): more rows than the TMEM accumulator ring
+# holds (8 blocks for 64 outputs, 32 for 16), runs that cross column blocks and
+# images, and, for 64 -> 64, the residual read from the staged input rows.
+@pytest.mark.parametrize("cin,nout,nimg,H,W", [(64, 16, 2, 320, 1024), (64, 64, 2, 200, 1024), (16, 64, 1, 400, 512)])
+def test_conv_long_runs_match_reference(cin, nout, nimg, H, W):
+    rng = np.random.default_rng(cin * 3 + nout + H)
+    x = bf16_round(rng.standard_normal((nimg, H, W, cin)))
+    w = rng.standard_normal((nout, cin, 3, 3)) / np.sqrt(9 * cin)
+    wq = bf16_round(w)
+    b = rng.standard_normal(nout) * 0.1
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    xd = to_dev(x, torch.bfloat16)
+    if cin == nout:
+        ao = torch.empty((nimg, H, W, nout), dtype=torch.bfloat16, device=dev)
+        S.conv3x3(xd, packed(w, cin, nout), nout, S.EPI_GELU, None, ao, bias=to_dev(b, torch.float32), aux0=xd,
+                  error_flag=err)
+    else:
+        out = torch.empty((nimg, H, W, nout), dtype=torch.float32, device=dev)
+        S.conv3x3(xd, packed(w, cin, nout), nout, S.EPI_LINEAR, out, bias=to_dev(b, torch.float32), error_flag=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    for i in range(nimg):
+        z = cnn.conv3x3(x[i], wq, b)
+        if cin == nout:
+            act = cnn.gelu(z) + x[i]
+            got = ao[i].float().cpu().numpy()
+            assert np.max(np.abs(got - act)) < 2 ** -8 * (np.abs(act).max() + 1.0) * 1.5
+        else:
+            got = out[i].cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(got - z)) <= 2e-5 * np.max(np.abs(z)) + 1e-6
+
+
 def test_transpose_flip_is_the_input_gradient():
     """Packing with transpose_flip turns the conv into its adjoint (dgrad)."""
     H, W, cin, nout = 3, 128, 64, 16  # forward layer 64 -> 16; dgrad maps 16 -> 64
