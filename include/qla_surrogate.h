@@ -5,7 +5,7 @@
  * problem (Sec. 4) by K QLA steps per call: Q_{t+K} = Q_t + s * f([Q_t, n]).
  * The paper has no learned component; the network only approximates the map
  * that the QLA step (Eq. 28) iterated K times defines, and plain QLA stays its
- * fallback and the judge of its error and energy (Eq. 27).
+ * fallback and the reference its error and energy (Eq. 27) are measured against.
  *
  * Conventions: activations are BF16 in NHWC order ([H][W][C], C contiguous)
  * on a periodic H x W lattice (circular padding, as the QLA lattice); all
