@@ -79,3 +79,30 @@ def test_create_rejects_bad_arguments_before_touching_a_gpu(lib):
     assert L.qla_create(4, 4, P(n), P(n), P(n), 0.0, None, None, ctypes.byref(ctx)) == 1
     assert L.qla_create(4, 4, P(n), P(n), P(n), 0.7, None, None, ctypes.byref(ctx)) == 1
     assert not ctx.value
+
+
+def test_conv_rejects_bad_arguments_without_gpu(lib):
+    """qla_conv3x3_bf16 checks sizes, channel pairs and epilogue operands on the
+    host and returns before any launch (the pointers below are never read)."""
+    from paper_2301_13601_gb300 import surrogate as S
+
+    L = S.lib()
+    p = ctypes.c_void_p(256)  # stand-in device pointer, never dereferenced on these paths
+    N = None
+
+    def call(x=p, nimg=1, H=4, W=128, cin=64, nout=64, epi=S.EPI_LINEAR, aux0=N, zprev=N, out0=p, out1=N, err=p):
+        return L.qla_conv3x3_bf16(x, nimg, H, W, cin, p, N, nout, epi, aux0, zprev, out0, out1, 1.0, err, N)
+
+    EINVAL, EUNSUPPORTED = 1, 6
+    assert call(x=N) == EINVAL
+    assert call(err=N) == EINVAL
+    assert call(nimg=0) == EINVAL
+    assert call(H=0) == EINVAL
+    assert call(W=100) == EINVAL and call(W=64) == EINVAL
+    assert call(nimg=2, H=1 << 15, W=1 << 15) == EINVAL  # more than 2^31 - 1 pixels
+    assert call(cin=32, nout=64) == EUNSUPPORTED and call(cin=16, nout=16) == EUNSUPPORTED
+    assert call(epi=4) == EINVAL and call(epi=-1) == EINVAL
+    assert call(out0=N) == EINVAL  # LINEAR writes out0
+    assert call(epi=S.EPI_GELU, out0=N, out1=N) == EINVAL  # GELU needs the activation output
+    assert call(epi=S.EPI_DGRAD, out1=p) == EINVAL  # DGRAD needs z_prev
+    assert call(epi=S.EPI_QUPDATE, nout=16) == EINVAL  # QUPDATE needs q_in
