@@ -106,3 +106,26 @@ def test_conv_rejects_bad_arguments_without_gpu(lib):
     assert call(epi=S.EPI_GELU, out0=N, out1=N) == EINVAL  # GELU needs the activation output
     assert call(epi=S.EPI_DGRAD, out1=p) == EINVAL  # DGRAD needs z_prev
     assert call(epi=S.EPI_QUPDATE, nout=16) == EINVAL  # QUPDATE needs q_in
+
+
+def test_pack_and_surrogate_create_reject_bad_arguments_without_gpu(lib):
+    """Host-side checks of qla_pack_conv_weights and qla_surrogate_create."""
+    from paper_2301_13601_gb300 import surrogate as S
+
+    L = S._net_lib()
+    p = ctypes.c_void_p(256)  # never dereferenced on these paths
+    EINVAL = 1
+    assert L.qla_pack_conv_weights(None, 64, 64, 64, 64, 0, p, None) == EINVAL
+    assert L.qla_pack_conv_weights(p, 64, 64, 64, 60, 0, p, None) == EINVAL  # padding not a multiple of 8
+    assert L.qla_pack_conv_weights(p, 64, 72, 64, 64, 0, p, None) == EINVAL  # cin above its padding
+    assert L.qla_pack_conv_weights(p, 6, 64, 16, 16, 1, p, None) == EINVAL  # adjoint: cin above nout_pad
+    assert L.qla_pack_conv_weights(p, 0, 64, 64, 64, 0, p, None) == EINVAL
+    h = ctypes.c_void_p()
+    assert L.qla_surrogate_create(None, ctypes.byref(h)) == EINVAL
+    for bad in (dict(W=100), dict(W=0), dict(H=0), dict(nimg=0), dict(K=0), dict(out_scale=0.0),
+                dict(out_scale=float("nan")), dict(out_scale=-1.0), dict(nimg=4, H=1 << 14, W=1 << 15)):
+        c = dict(nimg=1, H=64, W=128, K=16, out_scale=1.0 / 16, train=0, stream=None)
+        c.update(bad)
+        cfg = S.Config(**c)
+        assert L.qla_surrogate_create(ctypes.byref(cfg), ctypes.byref(h)) == EINVAL, bad
+        assert not h.value
