@@ -8,12 +8,22 @@ namespace qla {
 
 namespace {
 
+// FP32 rotation pair (t, s) for the three-shear collision of the sweep:
+// t = tan(a / 2) rounded to FP32, and s the FP32 value nearest to
+// 2t / (1 + t^2), the sine of the angle 2 atan(t) that t represents exactly.
+// The three shears (determinant exactly 1) are then a rotation to within one
+// rounding of s, and the angle differs from a by at most half an ulp of t.
+__device__ void shear_pair_f32(double ang, float &tf, float &sf) {
+    tf = (float)tan(0.5 * ang);
+    const double t = (double)tf;
+    sf = (float)(2.0 * t / (1.0 + t * t));
+}
+
 // FP32 (cos(a) - 1, sin(a)) pair chosen among FP32 values within a few ulps of
 // the correctly rounded ones so that (1 + m)^2 + s^2 - 1 (evaluated exactly in
-// FP64: every term is a product of two FP32 values) is as small as possible.
-// The angle changes by at most a few ulps of m / s, which is far below the
-// state's rounding; the norm of each rotation is then exact to ~1e-13, so the
-// rotations do not drift the energy (Eq. 27) systematically over 1e4 steps.
+// FP64: every term is a product of two FP32 values) is as small as possible:
+// each rotation then keeps the energy (Eq. 27) to ~1e-13, with the angle
+// changed by a few ulps of m and s at most.
 __device__ void tuned_pair_f32(double ang, float &mf, float &sf) {
     const double sh = sin(0.5 * ang);
     const double m = -2.0 * sh * sh;  // cos(ang) - 1 without cancellation
@@ -45,20 +55,28 @@ __device__ void tuned_pair_f32(double ang, float &mf, float &sf) {
     sf = __int_as_float(si + bds);
 }
 
-// Writes the pair (cos(ang) - 1, sin(ang)) of site i into pair plane `pair`.
+// How a pair is stored (see CoefPair and rot in the sweep): a collision of the
+// three-shear form (FP32 with the printed potentials: (tan(a/2), sin a)), a
+// rotation of the (cos - 1, sin) form (FP32: tuned for orthogonality) or a
+// printed potential row (cos a - 1, sin a). FP64 stores (cos a - 1, sin a)
+// for all.
+enum PairKind { PK_SHEAR, PK_ROTATION, PK_PRINTED_V };
+
 template <typename T>
-__device__ void store_rot(T *coef, size_t P, int pair, size_t i, double ang, bool tune) {
+__device__ void store_pair(T *coef, size_t P, int pair, size_t i, double ang, PairKind kind) {
     T *dst = coef + 2 * (size_t(pair) * P + i);
     if constexpr (sizeof(T) == 4) {
-        float mf, sf;
-        if (tune) {
-            tuned_pair_f32(ang, mf, sf);
+        float xf, sf;
+        if (kind == PK_SHEAR) {
+            shear_pair_f32(ang, xf, sf);
+        } else if (kind == PK_ROTATION) {
+            tuned_pair_f32(ang, xf, sf);
         } else {
             const double sh = sin(0.5 * ang);
-            mf = (float)(-2.0 * sh * sh);
+            xf = (float)(-2.0 * sh * sh);
             sf = (float)sin(ang);
         }
-        dst[0] = mf;
+        dst[0] = xf;
         dst[1] = sf;
     } else {
         const double sh = sin(0.5 * ang);
@@ -93,14 +111,15 @@ __global__ void coef_kernel(const double *__restrict__ n, T *__restrict__ coef, 
         const double b1 = delta * delta * dnx_dy / (vnx * vnx);
         const double b2 = delta * delta * dnz_dx / (vnz * vnz);
         const double b3 = delta * delta * dnz_dy / (vnz * vnz);
-        const bool tune_v = unitary != 0;  // the printed potentials are not rotations
-        store_rot<T>(coef, P, P_TM_C, i, th2, true);
-        store_rot<T>(coef, P, P_TE_CX, i, th1, true);
-        store_rot<T>(coef, P, P_TE_CY, i, th0, true);
-        store_rot<T>(coef, P, P_TM_VX, i, b2 * vscale, tune_v);
-        store_rot<T>(coef, P, P_TM_VY, i, b3 * vscale, tune_v);
-        store_rot<T>(coef, P, P_TE_VX, i, b0 * vscale, tune_v);
-        store_rot<T>(coef, P, P_TE_VY, i, b1 * vscale, tune_v);
+        const PairKind ck = unitary ? PK_ROTATION : PK_SHEAR;
+        const PairKind vk = unitary ? PK_ROTATION : PK_PRINTED_V;
+        store_pair<T>(coef, P, P_TM_C, i, th2, ck);
+        store_pair<T>(coef, P, P_TE_CX, i, th1, ck);
+        store_pair<T>(coef, P, P_TE_CY, i, th0, ck);
+        store_pair<T>(coef, P, P_TM_VX, i, b2 * vscale, vk);
+        store_pair<T>(coef, P, P_TM_VY, i, b3 * vscale, vk);
+        store_pair<T>(coef, P, P_TE_VX, i, b0 * vscale, vk);
+        store_pair<T>(coef, P, P_TE_VY, i, b1 * vscale, vk);
     }
 }
 

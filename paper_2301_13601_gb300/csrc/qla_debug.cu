@@ -13,26 +13,26 @@ namespace {
 
 constexpr int DBG_THREADS = 256;
 
-template <bool DAG, int SG, typename T>
+template <bool DAG, int SG, bool SHR, typename T>
 __device__ __forceinline__ void rot_pair(T *q, const typename Ar<T>::T2 *cp, long long P, long long i, int hub,
                                          int partner, int plane) {
     const typename Ar<T>::T2 c = cp[plane * P + i];
     T h = q[hub * P + i], p = q[partner * P + i];
-    rot<DAG, SG>(h, p, c.x, c.y);
+    rot<DAG, SG, SHR>(h, p, c.x, c.y);
     q[hub * P + i] = h;
     q[partner * P + i] = p;
 }
 
 // C_X (axis 0) or C_Y (axis 1) on both families, or their transposes.
-template <int AXIS, bool DAG, typename T>
+template <int AXIS, bool DAG, bool SHR, typename T>
 __global__ void __launch_bounds__(DBG_THREADS) collide_kernel(T *q, const typename Ar<T>::T2 *cp, long long P) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
         if (AXIS == 0) {
-            rot_pair<DAG, Fam<0>::SGX>(q, cp, P, i, Fam<0>::H, Fam<0>::PX, Fam<0>::CX);
-            rot_pair<DAG, Fam<1>::SGX>(q, cp, P, i, Fam<1>::H, Fam<1>::PX, Fam<1>::CX);
+            rot_pair<DAG, Fam<0>::SGX, SHR>(q, cp, P, i, Fam<0>::H, Fam<0>::PX, Fam<0>::CX);
+            rot_pair<DAG, Fam<1>::SGX, SHR>(q, cp, P, i, Fam<1>::H, Fam<1>::PX, Fam<1>::CX);
         } else {
-            rot_pair<DAG, Fam<0>::SGY>(q, cp, P, i, Fam<0>::H, Fam<0>::PY, Fam<0>::CY);
-            rot_pair<DAG, Fam<1>::SGY>(q, cp, P, i, Fam<1>::H, Fam<1>::PY, Fam<1>::CY);
+            rot_pair<DAG, Fam<0>::SGY, SHR>(q, cp, P, i, Fam<0>::H, Fam<0>::PY, Fam<0>::CY);
+            rot_pair<DAG, Fam<1>::SGY, SHR>(q, cp, P, i, Fam<1>::H, Fam<1>::PY, Fam<1>::CY);
         }
     }
 }
@@ -92,10 +92,25 @@ cudaError_t apply_t(int op, void *state, void *spare, const void *coef, int Nx, 
     const int blocks = int(std::min<long long>((P + DBG_THREADS - 1) / DBG_THREADS, 152LL * 16));
     *swapped = false;
     switch (op) {
-        case QLA_OP_CX: collide_kernel<0, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
-        case QLA_OP_CX_T: collide_kernel<0, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
-        case QLA_OP_CY: collide_kernel<1, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
-        case QLA_OP_CY_T: collide_kernel<1, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+        case QLA_OP_CX:
+        case QLA_OP_CX_T:
+        case QLA_OP_CY:
+        case QLA_OP_CY_T: {
+            // the collision form of the context's configuration (see rot)
+            const bool shear = shear_collisions<T, false>() && !unitary;
+            const int k = (op == QLA_OP_CX ? 0 : op == QLA_OP_CX_T ? 1 : op == QLA_OP_CY ? 2 : 3) + (shear ? 4 : 0);
+            switch (k) {
+                case 0: collide_kernel<0, false, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                case 1: collide_kernel<0, true, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                case 2: collide_kernel<1, false, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                case 3: collide_kernel<1, true, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                case 4: collide_kernel<0, false, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                case 5: collide_kernel<0, true, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                case 6: collide_kernel<1, false, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+                default: collide_kernel<1, true, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P); break;
+            }
+            break;
+        }
         case QLA_OP_VX:
             if (unitary) potential_kernel<0, true><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P);
             else potential_kernel<0, false><<<blocks, DBG_THREADS, 0, st>>>(q, cp, P);

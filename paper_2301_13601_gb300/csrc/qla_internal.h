@@ -8,11 +8,15 @@
 
 namespace qla {
 
-// Coefficient pair planes: NPAIR planes of [Ny][Nx] pairs (x = cos(a) - 1,
-// y = sin(a)), element type = state precision. The angle a is a collision
-// angle (Eq. 24) or an effective potential angle b (Eq. 25, scaled by 1/2
-// when interleaved (Eq. 28) and by 1/2 again for the unitary potentials).
-// Signs of the operators are applied by the kernels.
+// Coefficient pair planes: NPAIR planes of [Ny][Nx] pairs, element type =
+// state precision. The angle a is a collision angle (Eq. 24) or an effective
+// potential angle b (Eq. 25, scaled by 1/2 when interleaved (Eq. 28) and by
+// 1/2 again for the unitary potentials).
+// A collision pair is (x = tan(a/2), y = sin(a)) in FP32 with the printed
+// potentials (three-shear form) and (x = cos(a) - 1, y = sin(a)) otherwise; a
+// potential pair is (cos(b) - 1, sin(b)). FP32 pairs of the (cos - 1, sin)
+// form that are rotations (collisions and the unitary potentials) are tuned
+// for orthogonality. Signs of the operators are applied by the kernels.
 enum CoefPair {
     P_TM_C = 0,   // theta_2 (x and y collisions of the TM family)
     P_TM_VX = 1,  // beta_2 (V_X row q4)

@@ -33,9 +33,12 @@
 //    completion), per-lane cp.async elsewhere. (A bulk L2 prefetch two
 //    iterations ahead was measured to cost 18% on top of this staging and is
 //    not used.)
-//  * Rotations use the (cos-1, sin) form h' = h + (m h + s p): one rounding at
-//    the scale of h per output, with coefficients whose FP32 norm error is
-//    minimised at creation. Coefficients are stored as (m, s) pairs.
+//  * In FP32 with the printed potentials a collision is three shears
+//    (h += t p, p -= s h, h += t p with t = tan(theta/2): three FMAs, the
+//    determinant exactly 1); otherwise the (cos-1, sin) form
+//    h' = h + (m h + s p), one rounding at the scale of each output, with FP32
+//    pairs tuned at creation for orthogonality. Coefficients are stored as
+//    pairs of the form the kernel uses (see rot).
 #pragma once
 
 #include <cuda.h>
@@ -114,19 +117,47 @@ struct Fam<1> {
     static constexpr bool VX_HUB = true, VY_HUB = true;
 };
 
-// Collision C (DAG = false) or its transpose (DAG = true) on (h, p), with
-// m = cos(theta) - 1, s = sin(theta) and orientation SG:
-//   C:  h' = h + (m h + SG s p),   p' = p + (m p - SG s h)
-template <bool DAG, int SG, typename T>
+// Collision C (DAG = false) or its transpose (DAG = true) on (h, p) with
+// orientation SG: the rotation h' = c h + SG s p, p' = -SG s h + c p by the
+// angle theta (c = cos theta, s = sin theta).
+//  * SHEAR = false: pair (m, s) with m = cos(theta) - 1:
+//      h' = h + (m h + SG s p),   p' = p + (m p - SG s h)
+//    (one rounding at the scale of each output; six instructions).
+//  * SHEAR = true (FP32 with the printed potentials): pair (t, s) with
+//    t = tan(theta / 2), as three shears
+//      h1 = h + SG t p,  p' = p - SG s h1,  h' = h1 + SG t p'
+//    (three FMAs). Each shear has determinant exactly 1 whatever the rounding
+//    of t and s, so the rotation cannot scale the energy (Eq. 27) coherently;
+//    s is stored as the FP32 value nearest to 2t / (1 + t^2), which makes the
+//    shears a rotation to within one rounding of s, and the small remaining
+//    asymmetry biases the energy with opposite signs in C and its transpose,
+//    which alternate in Eq. 18 and Eq. 20.
+template <bool DAG, int SG, bool SHEAR, typename T>
 __device__ __forceinline__ void rot(T &h, T &p, T m, T s) {
     using A = Ar<T>;
     constexpr bool pos = (SG > 0) != DAG;
-    const T sp = A::mul(s, p);
-    const T sh = A::mul(s, h);
-    const T u = pos ? A::fma(m, h, sp) : A::fma(m, h, -sp);
-    const T v = pos ? A::fma(m, p, -sh) : A::fma(m, p, sh);
-    h = A::add(h, u);
-    p = A::add(p, v);
+    if constexpr (SHEAR) {
+        const T t = m;
+        h = pos ? A::fma(t, p, h) : A::fma(-t, p, h);
+        p = pos ? A::fma(-s, h, p) : A::fma(s, h, p);
+        h = pos ? A::fma(t, p, h) : A::fma(-t, p, h);
+    } else {
+        const T sp = A::mul(s, p);
+        const T sh = A::mul(s, h);
+        const T u = pos ? A::fma(m, h, sp) : A::fma(m, h, -sp);
+        const T v = pos ? A::fma(m, p, -sh) : A::fma(m, p, sh);
+        h = A::add(h, u);
+        p = A::add(p, v);
+    }
+}
+
+// Collision form of a configuration: three shears in FP32 with the printed
+// potentials; the (cos - 1, sin) form in FP64, and in FP32 with the unitary
+// potentials, where every operator is an exact rotation and the tuned pairs
+// keep the energy (Eq. 27) to FP32 rounding over 1e4 steps.
+template <typename T, bool UNIT>
+constexpr bool shear_collisions() {
+    return std::is_same<T, float>::value && !UNIT;
 }
 
 // Potential row: target' = target + (c target + TAU s source), c = cos(b) - 1,
@@ -364,6 +395,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     constexpr int NT = Cfg::NT;
     constexpr int NWARP = Cfg::NWARP;
     constexpr int NYS = L::NYS, NXS = L::NXS;
+    constexpr bool SHR = shear_collisions<T, UNIT>();
 
     T *const buf = reinterpret_cast<T *>(smem_raw);
     T2 *const yst = reinterpret_cast<T2 *>(smem_raw + L::STATE);
@@ -590,16 +622,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             constexpr int SG = Fm::SGX;
             // ops 1-8
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_left(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_right(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_right(h);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_left(h);
             T vc[LANE_COLS], vs[LANE_COLS];
             if constexpr (INTER) {
@@ -609,16 +641,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             }
             // ops 9-16
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_right(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_left(p);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<false, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_left(h);
 #pragma unroll
-            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG>(h[c], p[c], m[c], s[c]);
+            for (int c = 0; c < LANE_COLS; ++c) rot<true, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_right(h);
             if constexpr (INTER) {
 #pragma unroll
@@ -676,23 +708,23 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     T h = in[(0 * R + ir) * W_IN];
                     T p = in[(2 * R + ir) * W_IN];
                     const T px0 = in[(1 * R + ir) * W_IN];
-                    rot<true, SG>(h, p, m0, s0);                // op 1  C+   (row R)
+                    rot<true, SG, SHR>(h, p, m0, s0);                // op 1  C+   (row R)
                     { const T t = Y.S2; Y.S2 = p; p = t; }      // op 2  p <- p(r-1)
-                    rot<false, SG>(h, p, m0, s0);               // op 3  C    (row R)
+                    rot<false, SG, SHR>(h, p, m0, s0);               // op 3  C    (row R)
                     { const T t = Y.S4; Y.S4 = h; h = t; }      // op 4  p <- p(r+1): now row R-1
-                    rot<true, SG>(h, p, Y.m1, Y.s1);            // op 5  C+   (row R-1)
+                    rot<true, SG, SHR>(h, p, Y.m1, Y.s1);            // op 5  C+   (row R-1)
                     { const T t = Y.S6; Y.S6 = p; p = t; }      // op 6  h <- h(r+1): now row R-2
-                    rot<false, SG>(h, p, Y.m2, Y.s2);           // op 7  C    (row R-2)
+                    rot<false, SG, SHR>(h, p, Y.m2, Y.s2);           // op 7  C    (row R-2)
                     { const T t = Y.S8; Y.S8 = h; h = t; }      // op 8  h <- h(r-1)
                     if constexpr (INTER)
                         vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs2, Y.vc2);  // V_Y' (row R-2)
-                    rot<false, SG>(h, p, Y.m2, Y.s2);           // op 9  C    (row R-2)
+                    rot<false, SG, SHR>(h, p, Y.m2, Y.s2);           // op 9  C    (row R-2)
                     { const T t = Y.S10; Y.S10 = h; h = t; }    // op 10 p <- p(r+1): now row R-3
-                    rot<true, SG>(h, p, Y.m3, Y.s3);            // op 11 C+   (row R-3)
+                    rot<true, SG, SHR>(h, p, Y.m3, Y.s3);            // op 11 C+   (row R-3)
                     { const T t = Y.S12; Y.S12 = p; p = t; }    // op 12 p <- p(r-1)
-                    rot<false, SG>(h, p, Y.m3, Y.s3);           // op 13 C    (row R-3)
+                    rot<false, SG, SHR>(h, p, Y.m3, Y.s3);           // op 13 C    (row R-3)
                     { const T t = Y.S14; Y.S14 = h; h = t; }    // op 14 h <- h(r-1)
-                    rot<true, SG>(h, p, Y.m3, Y.s3);            // op 15 C+   (row R-3)
+                    rot<true, SG, SHR>(h, p, Y.m3, Y.s3);            // op 15 C+   (row R-3)
                     { const T t = Y.S16; Y.S16 = p; p = t; }    // op 16 h <- h(r+1): now row R-4
                     T px = Y.d3;
                     Y.d3 = Y.d2; Y.d2 = Y.d1; Y.d1 = Y.d0; Y.d0 = px0;

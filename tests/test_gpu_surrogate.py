@@ -232,7 +232,10 @@ def test_short_training_from_scratch_improves_held_out_error():
             inf.set_params(sur.get_params())
             after = T.evaluate(inf, w, 8, drift_tol=1e30)["rel_l2"]
     print("loss", hist, "held-out rel L2 before", before, "after", after)
-    assert hist[-1][1] < 0.3 * hist[1][1]
+    # each logged loss is that of one random batch of 4 pairs, so only the
+    # drop from the untrained network is asserted on it; the held-out rollout
+    # error is the deterministic criterion
+    assert hist[-1][1] < 0.02 * hist[0][1]
     assert after < before / 3
 
 

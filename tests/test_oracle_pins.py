@@ -402,6 +402,64 @@ def test_one_step_consistency_with_eq16(seq):
     assert p[-1] > 0.02 and abs(p[-1] / p[-2] - 1) < 0.05, p
 
 
+def eq26_beta_terms(q, n, mode):
+    """The refractive-index-gradient terms of Eq. 26 per unit delta^2/Delta t,
+    with spectral derivatives of the (band-limited) index fields:
+      dq3/dt = + (dn_z/dy / n_z^2) q2
+      dq4/dt = - (dn_z/dx / n_z^2) q2
+      dq5/dt = + (dn_y/dx / n_y^2) q1 - (dn_x/dy / n_x^2) q0
+    and zero for q0, q1, q2. With the unitary potentials (each coupled pair
+    rotated by half the angle) the target rows receive half of these terms
+    and the source rows the opposite half (a skew-symmetric generator)."""
+    nx, ny, nz = n
+    gx_ny = spectral_d(ny, 1) / ny ** 2
+    gy_nx = spectral_d(nx, 0) / nx ** 2
+    gx_nz = spectral_d(nz, 1) / nz ** 2
+    gy_nz = spectral_d(nz, 0) / nz ** 2
+    w = 1.0 if mode == oracle.POT_PAPER else 0.5
+    E = np.zeros_like(q)
+    E[3] = w * gy_nz * q[2]
+    E[4] = -w * gx_nz * q[2]
+    E[5] = w * (gx_ny * q[1] - gy_nx * q[0])
+    if mode == oracle.POT_UNITARY:
+        E[2] = w * (-gy_nz * q[3] + gx_nz * q[4])
+        E[1] = -w * gx_ny * q[5]
+        E[0] = w * gy_nx * q[5]
+    return E
+
+
+@pytest.mark.parametrize("mode", [oracle.POT_PAPER, oracle.POT_UNITARY])
+@pytest.mark.parametrize("seq", [oracle.SEQ_INTERLEAVED, oracle.SEQ_PLAIN])
+def test_potential_terms_match_eq26(seq, mode):
+    """Isolates what the external potentials add to one step: the step with the
+    Eq. 25 angles beta minus the same step with beta = 0 (same collision
+    angles), divided by delta^2, must converge at second order to the
+    index-gradient terms of Eq. 26, component by component. This fixes the
+    sign and the source component of every potential row (Eq. 21, Eq. 22 with
+    row 3 read as (sin b3, cos b3)), which the one-step residual above cannot
+    do for the printed potentials (their delta-independent defect hides a sign
+    error)."""
+    errs = []
+    for N in (32, 64, 128):
+        d = 1.0 / N
+        q0, n = _smooth_setup(N)
+        theta, beta = oracle.angles(n[0], n[1], n[2], d)
+        qa, qb = q0.copy(), q0.copy()
+        oracle.step(qa, theta, beta, seq, mode)
+        oracle.step(qb, theta, np.zeros_like(beta), seq, mode)
+        D = (qa - qb) / d ** 2
+        E = eq26_beta_terms(q0, n, mode)
+        scale = np.linalg.norm(E)
+        errs.append([np.linalg.norm(D[c] - E[c]) / (np.linalg.norm(E[c]) if np.any(E[c]) else scale)
+                     for c in range(6)])
+    errs = np.array(errs)
+    assert errs[-1].max() < 5e-3, errs
+    for c in range(6):
+        if errs[0, c] > 1e-13:
+            orders = np.log2(errs[:-1, c] / errs[1:, c])
+            assert np.all((orders > 1.9) & (orders < 2.1)), (c, errs[:, c])
+
+
 class _Yee:
     """Yee FDTD reference on an L x L periodic box for smooth analytic data."""
 
