@@ -221,7 +221,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     w = {"cylinders8192": media.workload_cylinders_8192, "ellipse2048": media.workload_ellipse_2048,
-         "cylinder256": media.workload_cylinder_256}[args.workload]()
+         "cylinder256": media.workload_cylinder_256,
+         "cylinders4096": lambda: media.workload_cylinders_8192(N=4096)}[args.workload]()
     n = w.medium()
     S = QLA_STEPS_PER_BENCH_STEP
     sim = Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
@@ -549,7 +550,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--steps-per-pass", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["cylinders8192", "ellipse2048", "cylinder256", "batch64", "surrogate1024"],
+    ap.add_argument("--workload", choices=["cylinders8192", "cylinders4096", "ellipse2048", "cylinder256", "batch64",
+                                           "surrogate1024"],
                     default="cylinders8192")
     ap.add_argument("--batch-step-scale", type=int, default=10, help="batch64: steps of each lattice divided by this")
     ap.add_argument("--chunk-rows", type=int, default=0)

@@ -33,8 +33,7 @@ struct BatchInst {
 // TMA tensor maps of one instance (as SweepParams, for both state buffers),
 // kept in device memory and read by the TMA unit from there.
 struct BatchMaps {
-    CUtensorMap st[2], st_r[2];
-    CUtensorMap cf, cf_r, cf_m;
+    SweepMaps m[2];  // per state buffer holding the input
 };
 
 struct BatchSched {
@@ -149,13 +148,11 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
         // read here by TMA loads (async proxy)
         asm volatile("fence.proxy.async;\n" ::: "memory");
         if (fam == 0)
-            sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, chunk, smem_raw, M ? &M->st[par] : nullptr,
-                                                    M ? &M->cf : nullptr, M ? &M->st_r[par] : nullptr,
-                                                    M ? &M->cf_r : nullptr, M && I.merged ? &M->cf_m : nullptr);
+            sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, chunk, smem_raw, M ? &M->m[par] : nullptr,
+                                                    I.merged != 0);
         else
-            sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, chunk, smem_raw, M ? &M->st[par] : nullptr,
-                                                    M ? &M->cf : nullptr, M ? &M->st_r[par] : nullptr,
-                                                    M ? &M->cf_r : nullptr, M && I.merged ? &M->cf_m : nullptr);
+            sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, chunk, smem_raw, M ? &M->m[par] : nullptr,
+                                                    I.merged != 0);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -396,17 +393,10 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
             a.Ny = I.Ny;
             a.w_valid = I.w_valid;
             a.chunk = I.chunk;
-            qla::SweepParams prm;
-            memset(&prm, 0, sizeof(prm));
-            ok = qla::make_sweep_maps(a, K, qla::kBatchRows, prm);
-            maps[k].st[par] = prm.tm_state;
-            maps[k].st_r[par] = prm.tm_state_r;
-            if (par == 0) {
-                maps[k].cf = prm.tm_coef;
-                maps[k].cf_r = prm.tm_coef_r;
-                maps[k].cf_m = prm.tm_coef_m;
-                I.merged = prm.merged;
-            }
+            int merged = 0;
+            memset(&maps[k].m[par], 0, sizeof(qla::SweepMaps));
+            ok = qla::make_sweep_maps(a, K, qla::kBatchRows, maps[k].m[par], &merged);
+            if (par == 0) I.merged = merged;
         }
         I.tma = ok ? 1 : 0;
     }

@@ -17,13 +17,15 @@ namespace qla {
 // potential pair is (cos(b) - 1, sin(b)). FP32 pairs of the (cos - 1, sin)
 // form that are rotations (collisions and the unitary potentials) are tuned
 // for orthogonality. Signs of the operators are applied by the kernels.
+// The order puts the two planes that the sweep copies together next to each
+// other: (V_X, C_X) for the x-pass and (C_Y, V_Y) for the y-pass of a family.
 enum CoefPair {
-    P_TM_C = 0,   // theta_2 (x and y collisions of the TM family)
-    P_TM_VX = 1,  // beta_2 (V_X row q4)
+    P_TM_VX = 0,  // beta_2 (V_X row q4)
+    P_TM_C = 1,   // theta_2 (x and y collisions of the TM family)
     P_TM_VY = 2,  // beta_3 (V_Y row q3)
-    P_TE_CX = 3,  // theta_1 (C_X pair q1, q5)
-    P_TE_CY = 4,  // theta_0 (C_Y pair q0, q5)
-    P_TE_VX = 5,  // beta_0 (V_X row q5)
+    P_TE_VX = 3,  // beta_0 (V_X row q5)
+    P_TE_CX = 4,  // theta_1 (C_X pair q1, q5)
+    P_TE_CY = 5,  // theta_0 (C_Y pair q0, q5)
     P_TE_VY = 6,  // beta_1 (V_Y row q5)
     NPAIR = 7
 };

@@ -54,23 +54,29 @@ namespace qla {
 constexpr int LANE_COLS = 8;
 constexpr int W_IN = 32 * LANE_COLS;
 
+// Tensor maps for the TMA loads of one FP32 pass: the input state viewed as
+// [6][Ny][Nx/8][8] floats with the 32-byte swizzle and the coefficient pairs
+// as [7][Ny][Nx/8][16] floats with the 64-byte swizzle. One box row (8 x 32,
+// resp. 16 x 32) is one 256-column strip row, landing in exactly the
+// XOR-swizzled layout of the shared row buffers (swz below).
+struct SweepMaps {
+    CUtensorMap state;     // one row of one component (blocks that wrap around y)
+    CUtensorMap state_r1;  // R rows of 1 component
+    CUtensorMap state_r2;  // R rows of 2 adjacent components
+    CUtensorMap state_r3;  // R rows of 3 adjacent components
+    CUtensorMap coef;      // one row of one pair plane
+    CUtensorMap coef_r;    // R rows of one pair plane
+    // The pair planes as [7][Ny / (R + 4)][R + 4][Nx/8][16] floats: one box
+    // (16 x 32 x R x K x n) holds the R-row blocks of all K levels of an
+    // iteration, which start R + 4 rows apart, of n adjacent planes (n = 1, 2);
+    // valid when merged != 0 (K > 1 and Ny a multiple of R + 4).
+    CUtensorMap coef_m1;
+    CUtensorMap coef_m2;
+};
+
 struct SweepParams {
     SweepArgs a;
-    // Tensor maps for the TMA loads (FP32, used when tma != 0): the input
-    // state viewed as [6][Ny][Nx/8][8] floats with the 32-byte swizzle and the
-    // coefficient pairs as [7][Ny][Nx/8][16] floats with the 64-byte swizzle.
-    // One box row (8 x 32, resp. 16 x 32) is one 256-column strip row, landing
-    // in exactly the XOR-swizzled layout of the shared row buffers (swz below).
-    // The *_r maps load R consecutive rows (a whole row block) per box; the
-    // one-row maps serve blocks that wrap around y.
-    CUtensorMap tm_state;
-    CUtensorMap tm_coef;
-    CUtensorMap tm_state_r;
-    CUtensorMap tm_coef_r;
-    // The coefficient pairs as [7][Ny / (R + 4)][R + 4][Nx/8][16] floats: one
-    // box (16 x 32 x R x K) holds the R-row blocks of all K levels of an
-    // iteration, which start R + 4 rows apart (used when merged != 0).
-    CUtensorMap tm_coef_m;
+    SweepMaps m;
     int tma;
     int merged;
     int tiles_fastest;  // grid x runs over the row tiles of a strip (else over the strips of a tile row)
@@ -102,12 +108,19 @@ struct Ar<double> {
 //     C_Y on (q0,q5): q5' = -s q0 + c q5 -> orientation -1; V_Y row q5 <- -sin b1 q0 (hub, -1)
 template <int FAM>
 struct Fam;
+// State planes sit in the shared row buffers in plane order, so that the
+// family's planes that are adjacent in global memory arrive in one TMA box:
+// SH, SPX, SPY are the buffer slots of the hub and the partners, and the
+// state boxes are (first plane, planes, first slot) per box (n1 = 0: none).
 template <>
 struct Fam<0> {
     static constexpr int H = 2, PX = 4, PY = 3;
     static constexpr int CX = P_TM_C, CY = P_TM_C, VX = P_TM_VX, VY = P_TM_VY;
     static constexpr int SGX = -1, SGY = +1, TX = -1, TY = +1;
     static constexpr bool VX_HUB = false, VY_HUB = false;
+    static constexpr int SH = 0, SPY = 1, SPX = 2;  // planes 2, 3, 4
+    static constexpr int B0 = 2, N0 = 3, B1 = 0, N1 = 0;
+    static constexpr int plane_of_slot(int slot) { return 2 + slot; }
 };
 template <>
 struct Fam<1> {
@@ -115,6 +128,9 @@ struct Fam<1> {
     static constexpr int CX = P_TE_CX, CY = P_TE_CY, VX = P_TE_VX, VY = P_TE_VY;
     static constexpr int SGX = +1, SGY = -1, TX = +1, TY = -1;
     static constexpr bool VX_HUB = true, VY_HUB = true;
+    static constexpr int SPY = 0, SPX = 1, SH = 2;  // planes 0, 1, 5
+    static constexpr int B0 = 0, N0 = 2, B1 = 5, N1 = 1;
+    static constexpr int plane_of_slot(int slot) { return slot < 2 ? slot : 5; }
 };
 
 // Collision C (DAG = false) or its transpose (DAG = true) on (h, p) with
@@ -179,6 +195,17 @@ template <int TAU, bool HUB, bool UNIT, typename T>
 __device__ __forceinline__ void vop_pair(T &h, T &p, T s, T c) {
     if (HUB) vop<TAU, UNIT>(h, p, s, c);
     else vop<TAU, UNIT>(p, h, s, c);
+}
+
+// Magnitude bits of a coefficient (zero for +0 and -0 only).
+template <typename T>
+__device__ __forceinline__ unsigned nzbits(T v) {
+    if constexpr (sizeof(T) == 4) {
+        return __float_as_uint(v) & 0x7fffffffu;
+    } else {
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull;
+        return unsigned(b) | unsigned(b >> 32);
+    }
 }
 
 // a(x) <- a(x-1) across the warp's 8*32 columns
@@ -383,11 +410,7 @@ struct YPipe {
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
 __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int chunk_idx, unsigned char *smem_raw,
-                                           const CUtensorMap *tm_state = nullptr,
-                                           const CUtensorMap *tm_coef = nullptr,
-                                           const CUtensorMap *tm_state_r = nullptr,
-                                           const CUtensorMap *tm_coef_r = nullptr,
-                                           const CUtensorMap *tm_coef_m = nullptr) {
+                                           const SweepMaps *M = nullptr, bool merged = false) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     using T2 = typename Ar<T>::T2;
@@ -396,6 +419,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     constexpr int NWARP = Cfg::NWARP;
     constexpr int NYS = L::NYS, NXS = L::NXS;
     constexpr bool SHR = shear_collisions<T, UNIT>();
+    // coefficient stash slots, in the order of the pair planes (so that a
+    // group's planes arrive in one TMA box): x-pass (Eq. 28) V_X then C_X,
+    // (Eq. 23) C_X; y-pass C_Y, V_Y (+ V_X for Eq. 23)
+    constexpr int XS_C = INTER ? 1 : 0, XS_V = 0;
+    static_assert(!INTER || (Fm::VX + 1 == Fm::CX && Fm::CY + 1 == Fm::VY), "pair planes of a copy group adjacent");
 
     T *const buf = reinterpret_cast<T *>(smem_raw);
     T2 *const yst = reinterpret_cast<T2 *>(smem_raw + L::STATE);
@@ -438,9 +466,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         return wrap_down(wrap_up(r0w + (it - itcur) * R - j * (R + 4) + ir, Ny), Ny);
     };
 
-    const T *const qh = qin + size_t(Fm::H) * P;
-    const T *const qpx = qin + size_t(Fm::PX) * P;
-    const T *const qpy = qin + size_t(Fm::PY) * P;
     const T2 *const pCX = cpairs + size_t(Fm::CX) * P;
     const T2 *const pCY = cpairs + size_t(Fm::CY) * P;
     const T2 *const pVX = cpairs + size_t(Fm::VX) * P;
@@ -451,9 +476,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     // level-0 state rows for iteration it (3 components x R rows)
     auto copy_state0 = [&](int it, int half) {
         for (int task = warp; task < 3 * R; task += NWARP) {
-            const int comp = task / R, ir = task % R;
-            const T *src = (comp == 0 ? qh : (comp == 1 ? qpx : qpy)) + size_t(growof(0, it, ir)) * Nx;
-            copy_strip_row(bufrow(0, half, comp, ir), src, xb, Nx, nowrap, vec, lane);
+            const int slot = task / R, ir = task % R;
+            const T *src = qin + size_t(Fm::plane_of_slot(slot)) * P + size_t(growof(0, it, ir)) * Nx;
+            copy_strip_row(bufrow(0, half, slot, ir), src, xb, Nx, nowrap, vec, lane);
         }
     };
     // x-pass coefficient rows of iteration it, all active levels
@@ -462,7 +487,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             const int j = task / (NXS * R), rem = task % (NXS * R);
             const int slot = rem / R, ir = rem % R;
             if (!active(j, it)) continue;
-            const T2 *plane = slot == 0 ? pCX : pVX;
+            const T2 *plane = slot == XS_C ? pCX : pVX;
             copy_strip_row(xstrow(j, slot, ir), plane + size_t(growof(j, it, ir)) * Nx, xb, Nx, nowrap, vec, lane);
         }
     };
@@ -479,65 +504,82 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     // TMA path (FP32, a strip that does not wrap around x, 8-column aligned).
     // Group X (x-pass coefficients of every active level and the level-0 state
     // rows) and group Y (y-pass coefficients) each complete on one mbarrier.
-    // Each box carries the R rows of one (level, plane) block, so a group is
-    // 3 + K * NXS (resp. K * NYS) loads, issued by lane 0 of as many warps:
-    // measured on GB300, per-row loads issued by one warp cost a quarter of the
-    // kernel's time, the issue itself being the bottleneck.
+    // A box carries whole R-row blocks: of all K levels and of the group's
+    // adjacent pair planes at once (V_X, C_X resp. C_Y, V_Y with Eq. 28), and of
+    // the family's adjacent state planes (TM: one box of 3 planes; TE: 2 + 1).
+    // An iteration then issues 3 (TM) or 4 (TE) loads, by lane 0 of as many
+    // warps: measured on GB300, each issue holds its warp for hundreds of
+    // cycles, so the number of issues, not the bytes, is what costs.
     uint64_t *const tbar = reinterpret_cast<uint64_t *>(smem_raw + L::BAR_OFF);
     bool use_tma = false;
     if constexpr (std::is_same<T, float>::value)
-        use_tma = tm_state != nullptr && tm_coef != nullptr && tm_state_r != nullptr && tm_coef_r != nullptr &&
-                  nowrap && (xb & 7) == 0 && (tc::smem_addr(smem_raw) & 1023u) == 0;
+        use_tma = M != nullptr && nowrap && (xb & 7) == 0 && (tc::smem_addr(smem_raw) & 1023u) == 0;
     uint32_t tph_x = 0, tph_y = 0;
     constexpr uint32_t SROW = W_IN * sizeof(T), CROW = W_IN * sizeof(T2);
-    // the R rows of a block from global row r0 on: one box, or R one-row boxes
-    // where the block wraps around y
-    auto tma_block = [&](void *dst, uint32_t row_bytes, const CUtensorMap *one, const CUtensorMap *blk, int j,
-                         int it, int plane, uint64_t *bar) {
+    // the R rows of a block (level j) of one pair plane: one box, or R one-row
+    // boxes where the block wraps around y
+    auto tma_block = [&](void *dst, int j, int it, int plane, uint64_t *bar) {
         const int r0 = growof(j, it, 0);
         if (r0 + R <= Ny) {
-            tma_row(dst, blk, xb >> 3, r0, plane, bar);
+            tma_row(dst, &M->coef_r, xb >> 3, r0, plane, bar);
         } else {
             for (int ir = 0; ir < R; ++ir)
-                tma_row(static_cast<unsigned char *>(dst) + ir * row_bytes, one, xb >> 3, growof(j, it, ir), plane,
+                tma_row(static_cast<unsigned char *>(dst) + ir * CROW, &M->coef, xb >> 3, growof(j, it, ir), plane,
                         bar);
         }
     };
-    // the blocks of one coefficient plane for all K levels: one merged box
-    // where they neither wrap around y nor straddle a group of R + 4 rows,
-    // else one box (or R one-row boxes) per level
-    const bool merge_ok = tm_coef_m != nullptr && K > 1;
-    auto tma_plane = [&](bool ystash, int slot, int it, int plane, uint64_t *bar) {
-        T2 *const top = ystash ? ystrow(K - 1, slot, 0) : xstrow(K - 1, slot, 0);
+    // the blocks of n adjacent pair planes (stash slots slot0..) for all K
+    // levels: one merged box where they neither wrap around y nor straddle a
+    // group of R + 4 rows, else one box (or R one-row boxes) per level and plane
+    const bool merge_ok = merged && K > 1;
+    auto tma_planes = [&](bool ystash, int slot0, int n, int it, int plane0, uint64_t *bar) {
         const int r_top = growof(K - 1, it, 0);
         const int b0 = r_top % (R + 4);
         if (merge_ok && r_top + (K - 1) * (R + 4) + R <= Ny && b0 <= 4) {
-            tma_box5(top, tm_coef_m, xb >> 3, b0, r_top / (R + 4), plane, bar);
+            T2 *const top = ystash ? ystrow(K - 1, slot0, 0) : xstrow(K - 1, slot0, 0);
+            tma_box5(top, n == 2 ? &M->coef_m2 : &M->coef_m1, xb >> 3, b0, r_top / (R + 4), plane0, bar);
         } else {
-            for (int j = 0; j < K; ++j)
-                tma_block(ystash ? ystrow(j, slot, 0) : xstrow(j, slot, 0), CROW, tm_coef, tm_coef_r, j, it, plane,
-                          bar);
+            for (int q = 0; q < n; ++q)
+                for (int j = 0; j < K; ++j)
+                    tma_block(ystash ? ystrow(j, slot0 + q, 0) : xstrow(j, slot0 + q, 0), j, it, plane0 + q, bar);
         }
     };
+    // level-0 state rows: planes p0 .. p0 + n - 1 into buffer slots s0 ..
+    auto tma_state = [&](int it, int half, int p0, int n, int s0, uint64_t *bar) {
+        const int r0 = growof(0, it, 0);
+        if (r0 + R <= Ny) {
+            const CUtensorMap *map = n == 3 ? &M->state_r3 : (n == 2 ? &M->state_r2 : &M->state_r1);
+            tma_row(bufrow(0, half, s0, 0), map, xb >> 3, r0, p0, bar);
+        } else {
+            for (int q = 0; q < n; ++q)
+                for (int ir = 0; ir < R; ++ir)
+                    tma_row(bufrow(0, half, s0 + q, ir), &M->state, xb >> 3, growof(0, it, ir), p0 + q, bar);
+        }
+    };
+    constexpr int NSB = Fm::N1 > 0 ? 2 : 1;  // state boxes of the family
     auto tma_group_x = [&](int it, bool with_state, int half) {
         // every level's blocks are loaded (an inactive level's are not read)
         const uint32_t row_bytes = uint32_t(K * NXS) * CROW + (with_state ? 3u * SROW : 0u);
         if (tid == 0) mbar_arrive_expect_tx(&tbar[0], uint32_t(R) * row_bytes);
-        const int ntask = NXS + (with_state ? 3 : 0);
+        const int ntask = 1 + (with_state ? NSB : 0);
         for (int t = warp + NWARP * lane; t < ntask; t += 32 * NWARP) {
-            if (t < NXS) {
-                tma_plane(false, t, it, t == 0 ? Fm::CX : Fm::VX, &tbar[0]);
+            if (t == 0) {
+                if constexpr (INTER) tma_planes(false, XS_V, 2, it, Fm::VX, &tbar[0]);
+                else tma_planes(false, XS_C, 1, it, Fm::CX, &tbar[0]);
+            } else if (t == 1) {
+                tma_state(it, half, Fm::B0, Fm::N0, 0, &tbar[0]);
             } else {
-                const int comp = t - NXS;
-                tma_block(bufrow(0, half, comp, 0), SROW, tm_state, tm_state_r, 0, it,
-                          comp == 0 ? Fm::H : (comp == 1 ? Fm::PX : Fm::PY), &tbar[0]);
+                tma_state(it, half, Fm::B1, Fm::N1, Fm::N0, &tbar[0]);
             }
         }
     };
     auto tma_group_y = [&](int it) {
         if (tid == 0) mbar_arrive_expect_tx(&tbar[1], uint32_t(R * K * NYS) * CROW);
-        for (int t = warp + NWARP * lane; t < NYS; t += 32 * NWARP)
-            tma_plane(true, t, it, t == 0 ? Fm::CY : (t == 1 ? Fm::VY : Fm::VX), &tbar[1]);
+        constexpr int ntask = INTER ? 1 : 2;
+        for (int t = warp + NWARP * lane; t < ntask; t += 32 * NWARP) {
+            if (t == 0) tma_planes(true, 0, 2, it, Fm::CY, &tbar[1]);  // C_Y, V_Y
+            else tma_planes(true, 2, 1, it, Fm::VX, &tbar[1]);         // V_X (Eq. 23)
+        }
     };
     // bounded wait for a copy group; a timeout sets the error flag (the
     // results of the launch are then invalid) instead of hanging
@@ -595,6 +637,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     YPipe<T> yp[NY];
 #pragma unroll
     for (int u = 0; u < NY; ++u) yp[u].zero();
+    bool vy_prev_on = false;  // the previous iteration's V_Y' pairs were nonzero for the warp
 
     for (int it = 0; it < nit; ++it) {
         const int cur = it & 1;
@@ -613,10 +656,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                 tma_wait(0, tph_x);
                 tc::fence_after_sync();
             }
-            T *rh = bufrow(j, cur, 0, ir);
-            T *rp = bufrow(j, cur, 1, ir);
+            T *rh = bufrow(j, cur, Fm::SH, ir);
+            T *rp = bufrow(j, cur, Fm::SPX, ir);
             T m[LANE_COLS], s[LANE_COLS], h[LANE_COLS], p[LANE_COLS];
-            sload8pair(m, s, xstrow(j, 0, ir), lane);
+            sload8pair(m, s, xstrow(j, XS_C, ir), lane);
             sload8(h, rh, lane);
             sload8(p, rp, lane);
             constexpr int SG = Fm::SGX;
@@ -633,11 +676,24 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
 #pragma unroll
             for (int c = 0; c < LANE_COLS; ++c) rot<false, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_left(h);
+            // V_X' is the identity where the potential angle is zero, i.e.
+            // wherever the index field is locally uniform (most of a lattice
+            // holding compact objects): a warp whose 256 columns all have zero
+            // pairs skips both applications (the result is unchanged but for
+            // the sign of a zero).
             T vc[LANE_COLS], vs[LANE_COLS];
+            bool vx_on = false;
             if constexpr (INTER) {
-                sload8pair(vc, vs, xstrow(j, 1, ir), lane);
+                sload8pair(vc, vs, xstrow(j, XS_V, ir), lane);
+                unsigned nz = 0;
 #pragma unroll
-                for (int c = 0; c < LANE_COLS; ++c) vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
+                for (int c = 0; c < LANE_COLS; ++c) nz |= nzbits(vc[c]) | nzbits(vs[c]);
+                vx_on = __any_sync(0xffffffffu, nz != 0u);
+                if (vx_on) {
+#pragma unroll
+                    for (int c = 0; c < LANE_COLS; ++c)
+                        vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
+                }
             }
             // ops 9-16
 #pragma unroll
@@ -653,8 +709,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             for (int c = 0; c < LANE_COLS; ++c) rot<true, SG, SHR>(h[c], p[c], m[c], s[c]);
             shift_from_right(h);
             if constexpr (INTER) {
+                if (vx_on) {
 #pragma unroll
-                for (int c = 0; c < LANE_COLS; ++c) vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
+                    for (int c = 0; c < LANE_COLS; ++c)
+                        vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
+                }
             }
             sstore8(rh, lane, h);
             sstore8(rp, lane, p);
@@ -692,8 +751,28 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             tma_wait(1, tph_y);
             tc::fence_after_sync();
         }
-        auto rows = [&](auto final_tag) {
+        // V_Y' skip (Eq. 28): the applications of this iteration use the V_Y
+        // pairs of the previous iteration's rows and of this one's; when all
+        // of them are zero for the warp (a locally uniform index field) the
+        // V_Y' rows, their loads and the delay line are skipped (the delay
+        // line then holds zeros already).
+        bool vy_on = true;
+        if constexpr (INTER) {
+            unsigned nz = 0;
+#pragma unroll
+            for (int u = 0; u < NY; ++u)
+#pragma unroll
+                for (int ir = 0; ir < R; ++ir) {
+                    const T2 v = ys_base[u][YSLOT + ir * W_IN];
+                    nz |= nzbits(v.x) | nzbits(v.y);
+                }
+            const bool cur_on = __any_sync(0xffffffffu, nz != 0u);
+            vy_on = cur_on || vy_prev_on;
+            vy_prev_on = cur_on;
+        }
+        auto rows = [&](auto final_tag, auto von_tag) {
             constexpr bool FINAL = decltype(final_tag)::value;
+            constexpr bool VON = decltype(von_tag)::value;  // V_Y' applied (always for Eq. 23)
 #pragma unroll
             for (int ir = 0; ir < R; ++ir) {
 #pragma unroll
@@ -703,11 +782,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     const T *in = st_base[u] + hin;
                     const T2 *ys = ys_base[u];
                     const T2 cy = ys[ir * W_IN];
-                    const T2 vy = ys[YSLOT + ir * W_IN];
+                    const T2 vy = VON ? ys[YSLOT + ir * W_IN] : T2{T(0), T(0)};
                     const T m0 = cy.x, s0 = cy.y;
-                    T h = in[(0 * R + ir) * W_IN];
-                    T p = in[(2 * R + ir) * W_IN];
-                    const T px0 = in[(1 * R + ir) * W_IN];
+                    T h = in[(Fm::SH * R + ir) * W_IN];
+                    T p = in[(Fm::SPY * R + ir) * W_IN];
+                    const T px0 = in[(Fm::SPX * R + ir) * W_IN];
                     rot<true, SG, SHR>(h, p, m0, s0);                // op 1  C+   (row R)
                     { const T t = Y.S2; Y.S2 = p; p = t; }      // op 2  p <- p(r-1)
                     rot<false, SG, SHR>(h, p, m0, s0);               // op 3  C    (row R)
@@ -716,7 +795,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     { const T t = Y.S6; Y.S6 = p; p = t; }      // op 6  h <- h(r+1): now row R-2
                     rot<false, SG, SHR>(h, p, Y.m2, Y.s2);           // op 7  C    (row R-2)
                     { const T t = Y.S8; Y.S8 = h; h = t; }      // op 8  h <- h(r-1)
-                    if constexpr (INTER)
+                    if constexpr (INTER && VON)
                         vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs2, Y.vc2);  // V_Y' (row R-2)
                     rot<false, SG, SHR>(h, p, Y.m2, Y.s2);           // op 9  C    (row R-2)
                     { const T t = Y.S10; Y.S10 = h; h = t; }    // op 10 p <- p(r+1): now row R-3
@@ -729,7 +808,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     T px = Y.d3;
                     Y.d3 = Y.d2; Y.d2 = Y.d1; Y.d1 = Y.d0; Y.d0 = px0;
                     if constexpr (INTER) {
-                        vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs4, Y.vc4);  // V_Y' (row R-4)
+                        if constexpr (VON) vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs4, Y.vc4);  // V_Y' (row R-4)
                     } else {
                         vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h, px, Y.ws4, Y.wc4);  // V_X  (row R-4)
                         vop_pair<Fm::TY, Fm::VY_HUB, UNIT>(h, p, Y.vs4, Y.vc4);   // V_Y  (row R-4)
@@ -740,8 +819,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                     Y.m3 = Y.m2; Y.s3 = Y.s2;
                     Y.m2 = Y.m1; Y.s2 = Y.s1;
                     Y.m1 = m0;   Y.s1 = s0;
-                    Y.vc4 = Y.vc3; Y.vs4 = Y.vs3; Y.vc3 = Y.vc2; Y.vs3 = Y.vs2;
-                    Y.vc2 = Y.vc1; Y.vs2 = Y.vs1; Y.vc1 = vy.x; Y.vs1 = vy.y;
+                    if constexpr (VON) {
+                        Y.vc4 = Y.vc3; Y.vs4 = Y.vs3; Y.vc3 = Y.vc2; Y.vs3 = Y.vs2;
+                        Y.vc2 = Y.vc1; Y.vs2 = Y.vs1; Y.vc1 = vy.x; Y.vs1 = vy.y;
+                    }
                     if (FINAL && u == NY - 1) {
                         const int rout = rout0 + ir;
                         if (col_ok && rout >= yb && rout < ye) {
@@ -752,15 +833,22 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
                         }
                     } else {
                         T *out = const_cast<T *>(st_base[u]) + LVL + hout;  // level j+1, other half
-                        out[(0 * R + ir) * W_IN] = h;
-                        out[(1 * R + ir) * W_IN] = px;
-                        out[(2 * R + ir) * W_IN] = p;
+                        out[(Fm::SH * R + ir) * W_IN] = h;
+                        out[(Fm::SPX * R + ir) * W_IN] = px;
+                        out[(Fm::SPY * R + ir) * W_IN] = p;
                     }
                 }
             }
         };
-        if (last_is_final) rows(std::integral_constant<bool, true>());
-        else rows(std::integral_constant<bool, false>());
+        using tru = std::integral_constant<bool, true>;
+        using fls = std::integral_constant<bool, false>;
+        if (last_is_final) {
+            if (vy_on) rows(tru(), tru());
+            else rows(tru(), fls());
+        } else {
+            if (vy_on) rows(fls(), tru());
+            else rows(fls(), fls());
+        }
         itcur = it + 1;
         r0w = wrap_down(r0w + R, Ny);
         if (use_tma) {
@@ -776,16 +864,13 @@ template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB)
     sweep_kernel(const __grid_constant__ SweepParams prm) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const CUtensorMap *ts = prm.tma ? &prm.tm_state : nullptr;
-    const CUtensorMap *tcf = prm.tma ? &prm.tm_coef : nullptr;
+    const SweepMaps *maps = prm.tma ? &prm.m : nullptr;
     const int strip = prm.tiles_fastest ? blockIdx.y : blockIdx.x;
     const int chunk = prm.tiles_fastest ? blockIdx.x : blockIdx.y;
     if (prm.a.fam0 + int(blockIdx.z) == 0)
-        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, strip, chunk, smem_raw, ts, tcf, &prm.tm_state_r,
-                                                &prm.tm_coef_r, prm.merged ? &prm.tm_coef_m : nullptr);
+        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, strip, chunk, smem_raw, maps, prm.merged != 0);
     else
-        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, strip, chunk, smem_raw, ts, tcf, &prm.tm_state_r,
-                                                &prm.tm_coef_r, prm.merged ? &prm.tm_coef_m : nullptr);
+        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, strip, chunk, smem_raw, maps, prm.merged != 0);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -808,47 +893,48 @@ inline EncodeTiledFn encode_tiled_fn() {
     return fn;
 }
 
-// Tensor maps of one FP32 pass (see SweepParams); false when TMA cannot be used
-// (Nx not a multiple of 8, no encoder), in which case the kernel copies with cp.async.
-inline bool make_sweep_maps(const SweepArgs &a, int K, int R, SweepParams &prm) {
+// Tensor maps of one FP32 pass (see SweepMaps); false when TMA cannot be used
+// (Nx not a multiple of 8, no encoder), in which case the kernel copies with
+// cp.async. *merged: the merged-level coefficient maps are valid.
+inline bool make_sweep_maps(const SweepArgs &a, int K, int R, SweepMaps &m, int *merged) {
     const EncodeTiledFn fn = encode_tiled_fn();
+    *merged = 0;
     if (!fn || a.Nx % 8 != 0) return false;
     const cuuint64_t Nx = cuuint64_t(a.Nx), Ny = cuuint64_t(a.Ny);
-    const cuuint32_t one[4] = {1, 1, 1, 1};
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
     const cuuint64_t sdim[4] = {8, Nx / 8, Ny, 6};
     const cuuint64_t sstr[3] = {32, Nx * 4, Nx * Ny * 4};
-    const cuuint32_t sbox[4] = {8, 32, 1, 1};
-    if (fn(&prm.tm_state, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.q_in), sdim, sstr, sbox, one,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    const cuuint32_t sboxr[4] = {8, 32, cuuint32_t(R), 1};
-    if (fn(&prm.tm_state_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.q_in), sdim, sstr, sboxr, one,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    auto state_map = [&](CUtensorMap *map, cuuint32_t rows, cuuint32_t comps) {
+        const cuuint32_t box[4] = {8, 32, rows, comps};
+        return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.q_in), sdim, sstr, box, one,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!state_map(&m.state, 1, 1) || !state_map(&m.state_r1, cuuint32_t(R), 1) ||
+        !state_map(&m.state_r2, cuuint32_t(R), 2) || !state_map(&m.state_r3, cuuint32_t(R), 3))
         return false;
     const cuuint64_t cdim[4] = {16, Nx / 8, Ny, cuuint64_t(NPAIR)};
     const cuuint64_t cstr[3] = {64, Nx * 8, Nx * Ny * 8};
-    const cuuint32_t cbox[4] = {16, 32, 1, 1};
-    const cuuint32_t cboxr[4] = {16, 32, cuuint32_t(R), 1};
-    if (fn(&prm.tm_coef_r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, cboxr, one,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
+    auto coef_map = [&](CUtensorMap *map, cuuint32_t rows) {
+        const cuuint32_t box[4] = {16, 32, rows, 1};
+        return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, box, one,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!coef_map(&m.coef, 1) || !coef_map(&m.coef_r, cuuint32_t(R))) return false;
     const cuuint64_t G = cuuint64_t(R + 4);
-    prm.merged = 0;
     if (K > 1 && Ny % G == 0) {
-        const cuuint32_t one5[5] = {1, 1, 1, 1, 1};
         const cuuint64_t mdim[5] = {16, Nx / 8, G, Ny / G, cuuint64_t(NPAIR)};
         const cuuint64_t mstr[4] = {64, Nx * 8, G * Nx * 8, Nx * Ny * 8};
-        const cuuint32_t mbox[5] = {16, 32, cuuint32_t(R), cuuint32_t(K), 1};
-        prm.merged = fn(&prm.tm_coef_m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(a.coef), mdim, mstr,
-                        mbox, one5, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        auto merged_map = [&](CUtensorMap *map, cuuint32_t planes) {
+            const cuuint32_t box[5] = {16, 32, cuuint32_t(R), cuuint32_t(K), planes};
+            return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(a.coef), mdim, mstr, box, one,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        *merged = (merged_map(&m.coef_m1, 1) && merged_map(&m.coef_m2, 2)) ? 1 : 0;
     }
-    return fn(&prm.tm_coef, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(a.coef), cdim, cstr, cbox, one,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return true;
 }
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
@@ -882,7 +968,8 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     SweepParams prm;
     memset(&prm, 0, sizeof(prm));
     prm.a = a;
-    if constexpr (std::is_same<T, float>::value) prm.tma = (a.error != nullptr && make_sweep_maps(a, K, R, prm)) ? 1 : 0;
+    if constexpr (std::is_same<T, float>::value)
+        prm.tma = (a.error != nullptr && make_sweep_maps(a, K, R, prm.m, &prm.merged)) ? 1 : 0;
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
     // CTA order. One 224 KB CTA per SM (K = 4): the tiles of a strip in a row,

@@ -145,20 +145,22 @@ def workload_ellipse_2048() -> Workload:
                     Pulse(POL_EY, 512.0, 40.0, 1.0))
 
 
-def workload_cylinders_8192(seed: int = 3) -> Workload:
+def workload_cylinders_8192(seed: int = 3, N: int = 8192) -> Workload:
     """8192^2, FP32, delta 0.02, 20000 steps; three seeded cylinders R in [100, 400],
-    n_i uniform in [1.1, 3.0], edge 8; E_z pulse sigma 100 at x0 1024."""
+    n_i uniform in [1.1, 3.0], edge 8; E_z pulse sigma 100 at x0 1024. With N < 8192
+    the same recipe with every length (radii, margins, pulse position and width)
+    scaled by N/8192 (a smaller case of the same kernel configuration)."""
     rng = np.random.default_rng(seed)
-    N = 8192
-    x0, sigma = 1024.0, 100.0
+    f = N / 8192.0
+    x0, sigma = 1024.0 * f, 100.0 * f
     objs = []
     for _ in range(3):
-        R = float(rng.uniform(100.0, 400.0))
+        R = float(rng.uniform(100.0, 400.0)) * f
         n = tuple(float(v) for v in rng.uniform(1.1, 3.0, size=3))
-        yc = float(rng.uniform(R + 64.0, N - R - 64.0))
-        xc = float(rng.uniform(x0 + 3 * sigma, x0 + 3 * sigma + 400.0)) + R
+        yc = float(rng.uniform(R + 64.0 * f, N - R - 64.0 * f))
+        xc = float(rng.uniform(x0 + 3 * sigma, x0 + 3 * sigma + 400.0 * f)) + R
         objs.append(Ellipse(xc, yc, R, R, 0.0, n, 8.0))
-    return Workload("cylinders8192_fp32", N, N, 0.02, 20000, objs, Pulse(POL_EZ, x0, sigma, 1.0))
+    return Workload(f"cylinders{N}_fp32", N, N, 0.02, 20000, objs, Pulse(POL_EZ, x0, sigma, 1.0))
 
 
 BATCH_SIDES = (256, 384, 512, 768, 1024, 1536, 2048)
