@@ -194,8 +194,10 @@ qla_status qla_diagnostics(qla_ctx *ctx, qla_diag *out);
  * lattice, Nx*Ny > 2^31-1, a NULL pointer or a bad precision returns
  * QLA_EINVAL without touching the GPU. CUDA failures return QLA_ECUDA.
  * Non-finite values return QLA_ENONFINITE with *out filled in.
- * The first call on each device looks up the array's device address (and may
- * load the module): make it before any stream capture begins. All calls share
+ * Each call looks up the array's device address on the current device (so a
+ * device reset or a re-created context is followed); the first call on a
+ * device may also load the module: make it before any stream capture begins.
+ * All calls share
  * the one array and it keeps the last call's contents (each call writes every
  * record it reads, so nothing needs clearing); calls whose kernels overlap on
  * the GPU (other streams, other host threads) race on it and must be

@@ -247,8 +247,6 @@ cudaError_t launch_divD(const void *q, int precision, const double *index, int N
 // ---------------------------------------------------------------------------
 #include <limits.h>
 
-#include <mutex>
-
 #include "../../include/qla.h"
 
 namespace qla {
@@ -256,8 +254,6 @@ namespace {
 
 constexpr int NOALLOC_ROWS_PER_BLOCK = 4;
 constexpr int NOALLOC_MAX_PARTIALS = 4096;  // lattices of at most 4096 * 4 = 16384 rows
-constexpr int NOALLOC_MAX_DEVICES = 64;
-
 struct NoallocScratch {
     Partial part[NOALLOC_MAX_PARTIALS];
     DiagResult result;
@@ -265,26 +261,17 @@ struct NoallocScratch {
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
-std::mutex g_noalloc_mu;
-NoallocScratch *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-
 // Device address of the array on the current device. In host code the
 // symbol g_noalloc_scratch is only a host-side stand-in, so the address is
-// looked up once per device (the first call on each device does this, and may
-// load the module; make that first call before any stream capture).
+// looked up on every call: a cached address would go stale after a device
+// reset or a re-created primary context, when the module reloads elsewhere.
+// The first call on a device may load the module: make it before any stream
+// capture.
 cudaError_t noalloc_scratch(NoallocScratch **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<NoallocScratch *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<NoallocScratch *>(p);
     return cudaSuccess;
 }
 

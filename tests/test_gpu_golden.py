@@ -7,18 +7,23 @@ tests/golden/make_golden.py, which calls only the FP64 CPU oracle: energy
 
 Tolerances (targets: FP32 relative L2 <= 1e-4 after 1e4 steps, energy within
 1e-6 of E(0), FP64 mode within 1e-12):
-  * FP32 relative L2 <= 1e-4 (met with margin).
-  * FP32 |E_gpu - E_oracle| / E(0) <= 5e-6 with the printed potentials. The
-    FP32 state rounding (~64 roundings of 2^-24 per component and step) is
-    amplified where the printed, non-unitary potentials make the energy grow
-    (+6.6% over this run); the same rounding stays below 1e-6 when every
-    operator is orthogonal (test_unitary_fp32_energy_drift_full_length).
+  * FP32 relative L2 <= 1e-4 (met with margin: 1.1e-5).
+  * FP32 |E_gpu - E_oracle| / E(0) <= 2.5e-6 with the printed potentials: the
+    measured 2.07e-6 with a 20% margin, so that a regression shows; the 1e-6
+    target is not met. The FP32 state rounding is amplified where the printed,
+    non-unitary potentials make the energy grow (+6.6% over this run); the same
+    rounding stays below 1e-6 when every operator is orthogonal
+    (test_unitary_fp32_energy_drift_full_length).
   * FP64 relative L2 <= 2e-11 at 1e4 steps: the oracle evaluates cos and sin
-    of each angle in double and rounds them separately, so its rotations are
-    orthogonal only to ~1e-16, coherently over the 16 rotations of a step;
-    after 1e4 steps that alone bounds the agreement by ~16 * 1e4 * 1.1e-16 =
-    1.8e-11. Over the 400-step cylinder workload the bound 1e-12 holds
-    (test_gpu_parity.py).
+    of each angle in double and rounds them separately, so each of its
+    rotations scales its pair's norm squared by 1 + d with d ~ 1e-16, the same
+    at every step: in vacuum at delta = 0.05 its energy drifts by 12 d T =
+    1.2e-11 after 1e4 steps, i.e. 6e-12 in relative L2 away from an exactly
+    norm-preserving evolution (pinned on the CPU by
+    test_fp64_rotation_defect_drifts_the_energy_coherently, and on the GPU by
+    test_fp64_vacuum_energy_is_conserved_where_the_oracle_drifts below, the
+    GPU's FP64 pairs being orthogonal to ~1e-20). Over the 400-step cylinder
+    workload the bound 1e-12 holds (test_gpu_parity.py).
 """
 import os
 
@@ -66,7 +71,7 @@ def test_ellipse_2048_fp32_full_length(golden):
     rl = {s: rel_l2(got[f"q_s{s}"], golden[f"q_s{s}"]) for s in (1000, 10000)}
     print(f"fp32: max energy difference {drift.max():.3e} of E(0); rel L2 {rl}")
     assert rl[10000] <= 1e-4 and rl[1000] <= 1e-4
-    assert drift.max() <= 5e-6
+    assert drift.max() <= 2.5e-6
 
 
 def test_ellipse_2048_fp64_full_length(golden):
@@ -87,3 +92,34 @@ def test_unitary_fp32_energy_drift_full_length():
     drift = np.abs(got["energy"] / got["energy"][0] - 1)
     print(f"fp32 unitary: max |E/E(0) - 1| = {drift.max():.3e}")
     assert drift.max() <= 1e-6
+
+
+def test_fp64_vacuum_energy_is_conserved_where_the_oracle_drifts():
+    """The 1D vacuum run of the oracle's rotation-defect pin (E_y pulse, delta
+    0.05, 2000 steps): the oracle's energy drifts by 12 d T = 2.5e-12, the GPU's
+    FP64 mode keeps it to rounding noise, and their states differ by half the
+    oracle's drift in relative L2 (the norm ratio), so the FP64 gap to the
+    oracle at 1e4 steps is the oracle's own arithmetic."""
+    import math
+    from fractions import Fraction
+
+    import oracle
+
+    Nx, T, delta = 256, 2000, 0.05
+    n = np.ones((8, Nx))
+    q0 = oracle.init_pulse(Nx, 8, oracle.POL_EY, 128.0, 10.0, 1.0)
+    ref = oracle.simulate(n, n, n, delta, q0, T)
+    with Simulation(n, n, n, delta, precision="fp64") as sim:
+        sim.set_fields(q0)
+        sim.step(T)
+        got = sim.get_fields()
+    E0 = oracle.energy(q0)
+    c, s = math.cos(delta / 4), math.sin(delta / 4)
+    d = float(Fraction(c) ** 2 + Fraction(s) ** 2 - 1)
+    drift_oracle = oracle.energy(ref) / E0 - 1
+    drift_gpu = oracle.energy(got) / E0 - 1
+    print(f"energy drift: oracle {drift_oracle:.3e} (12 d T = {12 * d * T:.3e}), GPU FP64 {drift_gpu:.3e}; "
+          f"rel L2 {rel_l2(got, ref):.3e}")
+    assert abs(drift_oracle / (12 * d * T) - 1) < 0.02
+    assert abs(drift_gpu) < 0.05 * abs(drift_oracle)
+    assert abs(rel_l2(got, ref) / abs(drift_oracle / 2) - 1) < 0.1

@@ -78,10 +78,8 @@ def test_noalloc_after_a_larger_call_and_nonfinite():
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
-    L = load_library()
-    d = Diag()
-    dummy = ctypes.c_void_p(16)  # never dereferenced: the size check comes first
-    assert L.qla_diagnostics_noalloc(dummy, FP32, 8, 16385, None, ctypes.byref(d)) == 1
-    assert L.qla_diagnostics_noalloc(dummy, FP64, 70000, 70000, None, ctypes.byref(d)) == 1
-    assert L.qla_diagnostics_noalloc(dummy, 7, 8, 8, None, ctypes.byref(d)) == 1
-    assert L.qla_diagnostics_noalloc(None, FP32, 8, 8, None, ctypes.byref(d)) == 1
+    """Size and argument checks come before any use of the device (run with no
+    visible GPU, so that a missing check cannot reach one)."""
+    import host_checks
+
+    host_checks.run_without_gpu("noalloc_rejects_sizes_beyond_its_scratch")
