@@ -318,6 +318,7 @@ def run_ours(args):
     }
     if not args.skip_extras:
         line["single_family"] = single_family_report(w, args, peak, peak_kind)
+        line["batch"] = batch_report(args, peak, peak_kind)
     if not args.skip_extras and not args.skip_surrogate:
         line["surrogate"] = surrogate_report()
     print(json.dumps(line), flush=True)
@@ -359,6 +360,53 @@ def single_family_report(w, args, peak, peak_kind, steps: int = 5):
             "bytes_per_site_update": alg, "bandwidth_equivalent_frac": value * alg / 1e9 / peak,
             "peak_kind": peak_kind, "note": "same bench step (100 QLA steps + diagnostics); the other family's "
             "planes are zero and stay zero (Eq. 17-22 never couple the families)"}
+
+
+def batch_instances(args):
+    """The 64-lattice workload (sides 256-2048, 2000-8000 steps each), every
+    lattice's step count divided by --batch-step-scale (a bench step stays
+    well under a second)."""
+    from paper_2301_13601_gb300 import media
+
+    ws = media.workload_batch64()
+    inst = []
+    for w in ws:
+        steps = max(4, (w.steps // args.batch_step_scale) // 4 * 4)
+        inst.append({"n": w.medium(), "delta": w.delta, "nsteps": steps,
+                     "pulse": ("Ez" if w.pulse.pol == media.POL_EZ else "Ey", w.pulse.x0, w.pulse.sigma, 1.0)})
+        if args.chunk_rows:
+            inst[-1]["chunk_rows"] = args.chunk_rows
+    return ws, inst
+
+
+def batch_report(args, peak, peak_kind, steps: int = 3):
+    """The batched workload in one persistent CUDA-graph launch per bench step,
+    with the steps per pass and rows per tile chosen by the autotuner (timed
+    candidates, cached per GPU, kernel version and batch shape)."""
+    import torch
+
+    from paper_2301_13601_gb300.qla import Batch
+
+    ws, inst = batch_instances(args)
+    t_tune = time.perf_counter()
+    with Batch(inst, steps_per_pass=0) as b:
+        t_tune = time.perf_counter() - t_tune
+        info = b.info()
+        b.run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            b.run()
+        el = time.perf_counter() - t0
+        tuned = dict(b.tuned)
+    value = info["site_updates"] * steps / el
+    return {"workload": f"batch64: {len(inst)} lattices, sides {sorted({w.Nx for w in ws})}, "
+                        f"{min(i['nsteps'] for i in inst)}-{max(i['nsteps'] for i in inst)} QLA steps each per run",
+            "value": value, "unit": UNIT, "ms_per_run": 1e3 * el / steps, "runs": steps,
+            "bandwidth_equivalent_frac": value * BYTES_PER_SITE_UPDATE / 1e9 / peak, "peak_kind": peak_kind,
+            "steps_per_pass": info["steps_per_pass"], "chunk_rows": tuned.get("chunk_rows"),
+            "autotuned": True, "autotune_seconds": t_tune, "work_items": info["work_items"],
+            "launch": "one persistent kernel in a CUDA graph per run (synchronous)"}
 
 
 SURROGATE_CHECKPOINT = os.path.join(ROOT, "paper_2301_13601_gb300", "checkpoints", "surrogate_k16.npz")
@@ -427,11 +475,37 @@ def surrogate_report(calls: int = 250, seed: int = 7):
         # steps per call at which one forward costs as much as plain QLA for those steps
         "break_even_K": meta["K"] * r["forward_seconds_per_call"] / r["qla_seconds_per_K"],
         "variants": variants,
+        "training_step_ms": time_training(params, meta),
+        "training_batch": "4 x 512x256 (loss, full gradient on the tensor cores, Adam)",
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                      "frac": achieved / bf16, "peak_kind": "measured" if peaks.get("bf16_tflops") else "fallback",
                      "kernel": "conv3x3_tc_kernel (6 layers, one forward call)",
                      "flops": "2 x padded MACs: 9 x (16x64 + 4 x 64x64 + 64x16) per site"},
     }
+
+
+def time_training(params, meta, warmup: int = 3, steps: int = 10) -> float:
+    """ms per surrogate training step (loss, full gradient and Adam on a batch
+    of 4 lattices of 512x256), CUDA events on the surrogate's stream."""
+    import torch
+
+    from paper_2301_13601_gb300 import surrogate as S
+
+    with S.Surrogate(256, 512, nimg=4, K=meta["K"], out_scale=meta["out_scale"], train=True) as tr:
+        tr.set_params(params)
+        qa = torch.randn((4, 6, 256, 512), device="cuda")
+        na = torch.rand((4, 3, 256, 512), device="cuda") * 2 + 1
+        qb = qa * 1.01
+        for _ in range(warmup):
+            tr.train_step(qa, na, qb, 1e-6)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(tr.stream)
+        for _ in range(steps):
+            tr.train_step(qa, na, qb, 1e-6)
+        e1.record(tr.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
 
 
 def run_surrogate(args):
@@ -468,21 +542,7 @@ def run_surrogate(args):
         e1.synchronize()
         fwd_ms = e0.elapsed_time(e1) / args.steps
         flops = sur.info()["flops_per_call"]
-    with S.Surrogate(256, 512, nimg=4, K=meta["K"], out_scale=meta["out_scale"], train=True) as tr:
-        tr.set_params(params)
-        qa = torch.randn((4, 6, 256, 512), device="cuda")
-        na = torch.rand((4, 3, 256, 512), device="cuda") * 2 + 1
-        qb = qa * 1.01
-        for _ in range(args.warmup):
-            tr.train_step(qa, na, qb, 1e-6)
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record(tr.stream)
-        for _ in range(args.steps):
-            tr.train_step(qa, na, qb, 1e-6)
-        e1.record(tr.stream)
-        e1.synchronize()
-        train_ms = e0.elapsed_time(e1) / args.steps
+    train_ms = time_training(params, meta, args.warmup, args.steps)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -509,20 +569,15 @@ def run_batch(args):
     import torch
 
     from paper_2301_13601_gb300 import build as _build
-    from paper_2301_13601_gb300 import media
     from paper_2301_13601_gb300.qla import Batch
 
     _build.build()
-    ws = media.workload_batch64()
-    K = args.steps_per_pass or 4
-    inst = []
-    for w in ws:
-        steps = max(K, (w.steps // args.batch_step_scale) // K * K)
-        inst.append({"n": w.medium(), "delta": w.delta, "nsteps": steps,
-                     "pulse": ("Ez" if w.pulse.pol == media.POL_EZ else "Ey", w.pulse.x0, w.pulse.sigma, 1.0),
-                     "chunk_rows": args.chunk_rows})
-    with Batch(inst, steps_per_pass=K) as b:
+    ws, inst = batch_instances(args)
+    # --steps-per-pass 0 (the default): the autotuner chooses steps per pass and tile rows
+    with Batch(inst, steps_per_pass=args.steps_per_pass) as b:
         info = b.info()
+        K = info["steps_per_pass"]
+        tuned = b.tuned
         for _ in range(args.warmup):
             b.run()
         torch.cuda.synchronize()
@@ -537,7 +592,9 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch64", "lattices": len(inst), "sides": sorted({w.Nx for w in ws}),
                        "qla_steps_per_lattice": f"{min(i['nsteps'] for i in inst)}-{max(i['nsteps'] for i in inst)}",
-                       "steps_per_pass": K, "work_items": info["work_items"], "launch": "one persistent kernel in a CUDA graph"},
+                       "steps_per_pass": K, "chunk_rows": (tuned or {}).get("chunk_rows", args.chunk_rows),
+                       "autotuned": tuned is not None, "work_items": info["work_items"],
+                       "launch": "one persistent kernel in a CUDA graph"},
             "bandwidth_equivalent_frac": value * BYTES_PER_SITE_UPDATE / 1e9 / peak, "peak_kind": peak_kind}
     print(json.dumps(line), flush=True)
 

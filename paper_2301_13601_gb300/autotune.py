@@ -38,8 +38,21 @@ def save_cache(cache: dict, path: Optional[str] = None) -> None:
     os.replace(tmp, p)
 
 
+def kernel_version() -> str:
+    """sha256 prefix of the sweep kernel's source: cached choices of an older
+    kernel are not reused."""
+    import hashlib
+
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "qla_sweep.cuh")
+    try:
+        with open(src, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:12]
+    except OSError:
+        return "unknown"
+
+
 def single_key(Nx: int, Ny: int, precision: str, sequence: str, potential: str, gpu: str) -> str:
-    return f"single/{gpu}/{precision}/{sequence}/{potential}/{Nx}x{Ny}"
+    return f"single/{gpu}/{kernel_version()}/{precision}/{sequence}/{potential}/{Nx}x{Ny}"
 
 
 def chunk_candidates(Ny: int, K: int) -> List[int]:
@@ -109,8 +122,9 @@ def tune_single(n_x, n_y, n_z, delta: float, precision: str = "fp32", sequence: 
     return entry
 
 
-def tune_batch(instances: List[dict], ks: Sequence[int] = (2, 4), chunks: Sequence[int] = (128, 256, 512, 1024),
-               step_scale: int = 8, use_cache: bool = True) -> dict:
+def tune_batch(instances: List[dict], ks: Sequence[int] = (2, 4), chunks: Sequence[int] = (256, 512, 768, 1024),
+               step_scale: int = 8, use_cache: bool = True, sequence: str = "interleaved",
+               potential: str = "paper") -> dict:
     """Pick steps per pass and one rows-per-tile value for a batch by timing a
     shortened copy of it (every lattice run for nsteps/step_scale steps)."""
     import torch
@@ -121,7 +135,8 @@ def tune_batch(instances: List[dict], ks: Sequence[int] = (2, 4), chunks: Sequen
     sig = ",".join(f"{ins['n'][0].shape[1]}x{ins['n'][0].shape[0]}:{ins['nsteps']}" for ins in instances)
     import hashlib
 
-    key = f"batch/{gpu}/{hashlib.sha256(sig.encode()).hexdigest()[:16]}"
+    key = (f"batch/{gpu}/{kernel_version()}/{sequence}/{potential}/"
+           f"{hashlib.sha256(sig.encode()).hexdigest()[:16]}")
     cache = load_cache() if use_cache else {}
     if key in cache:
         return cache[key]
@@ -135,7 +150,7 @@ def tune_batch(instances: List[dict], ks: Sequence[int] = (2, 4), chunks: Sequen
                 d["nsteps"] = s
                 d["chunk_rows"] = ch
                 short.append(d)
-            with Batch(short, steps_per_pass=K) as b:
+            with Batch(short, steps_per_pass=K, sequence=sequence, potential=potential) as b:
                 b.run()  # warm-up (graph capture)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()

@@ -370,6 +370,9 @@ class Batch:
     instances: list of dicts with keys n (tuple of three (Ny, Nx) arrays), delta,
     nsteps, and optionally pulse=(polarization 'Ez'/'Ey', x0, sigma, amplitude)
     and chunk_rows.
+    steps_per_pass = 0 lets the autotuner (autotune.tune_batch, cached per GPU
+    and batch shape) choose the steps per pass and the rows per tile of the
+    instances that do not set chunk_rows; the choice is kept in self.tuned.
     """
 
     def __init__(self, instances, steps_per_pass: int = 4, sequence="interleaved", potential="paper",
@@ -378,6 +381,14 @@ class Batch:
 
         if not torch.cuda.is_available():
             raise RuntimeError("libqla needs a CUDA GPU; no CPU fallback exists")
+        self.tuned = None
+        if int(steps_per_pass) == 0:
+            from .autotune import tune_batch
+
+            self.tuned = tune_batch(instances, sequence=sequence, potential=potential)
+            steps_per_pass = int(self.tuned["steps_per_pass"])
+            instances = [dict(ins, chunk_rows=ins.get("chunk_rows") or int(self.tuned["chunk_rows"]))
+                         for ins in instances]
         L = load_library()
         _batch_sigs(L)
         self._L = L

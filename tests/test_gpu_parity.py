@@ -284,3 +284,36 @@ def test_cylinders_8192_sampled_parity():
         b = ref[:, H - r:H + r + 1, H - r:H + r + 1]
         scale = max(np.abs(b).max(), 1e-3)
         assert np.abs(a - b).max() <= 2e-6 * scale + 1e-12, (yc, xc)
+
+
+def test_cylinders_8192_sampled_parity_200_steps():
+    """The first 200 steps of the 8192^2 workload in the benchmark's launch
+    configuration, on five sampled windows where the pulse is (the dependency
+    window after 200 steps is 1601^2 sites): the pulse flank, a tile seam, a
+    strip seam, the periodic y-wrap and the pulse's far flank. FP32 bound:
+    about 64 roundings of 2^-24 per component and step, a random walk of
+    6e-8 * sqrt(64 * 200) = 7e-6 of the local amplitude; 1e-5 is asserted."""
+    w = media.workload_cylinders_8192()
+    n = w.medium()
+    steps = 200
+    with Simulation(*n, w.delta, precision="fp32") as sim:
+        assert sim.steps_per_pass == 2
+        ch = sim.chunk_rows
+        sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+        q0 = sim.get_fields()
+        sim.step(steps)
+        got = sim.get_fields(dtype=np.float32)
+    H = 4 * steps + 8
+    x0 = int(w.pulse.x0)
+    samples = [(4096, x0 + 60), (5 * ch, x0 - 40), (3000, 960), (0, x0 + 10), (8191, x0 - 120)]
+    for yc, xc in samples:
+        nw = tuple(window(a, yc, xc, H) for a in n)
+        qw = window(q0, yc, xc, H)
+        ref = oracle_run(nw, qw, w.delta, steps)
+        r = 3
+        a = window(got, yc, xc, r)
+        b = ref[:, H - r:H + r + 1, H - r:H + r + 1]
+        scale = max(np.abs(b).max(), 1e-3)
+        err = np.abs(a - b).max() / scale
+        print(f"window ({yc}, {xc}): max error {err:.2e} of the local amplitude {scale:.3e}")
+        assert err <= 1e-5, (yc, xc)
