@@ -113,9 +113,9 @@ int default_steps_per_pass(int precision, int Nx, int Ny) {
 // most max_auto_chunk(K) rows. The caps are measured, not modelled: on the
 // 8192^2 workload tiles of 512-1280 rows (K = 4) beat the few-wave splits the
 // wave model alone prefers (39-40 G vs 36 G for 4096 rows), and with K = 2
-// (two CTAs per SM) tiles of 192-256 rows run 65.4-66.3 G against 64.5 G for
-// 320 and 60.8 G for 512 (the model then picks 216).
-int max_auto_chunk(int K) { return K == 2 ? 256 : 1024; }
+// (two CTAs per SM) tiles of 192-200 rows run 74.7 G against 74.3 G for 176,
+// 73.9 G for 216, 73.7 G for 232 and 72.8 G for 256 (the model then picks 192).
+int max_auto_chunk(int K) { return K == 2 ? 200 : 1024; }
 
 int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
     const int kMaxAutoChunk = max_auto_chunk(K);

@@ -110,6 +110,78 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial(const T *__restrict
     block_reduce_write(Partial{e.s, e.c, d.s, d.c, dmax, bmax, nf, 0ull}, part);
 }
 
+// Exact FP32 -> FP64 conversion on the integer pipe (this kernel is bound by
+// GB300's FP64 pipe, which also executes the hardware conversion): zero and
+// normal values by rebiasing the exponent and widening the mantissa; subnormal,
+// infinite and NaN values take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned e = (u >> 23) & 0xffu;
+    const bool zero = (u << 1) == 0u;
+    if (zero || e - 1u < 254u) {
+        const unsigned mag = zero ? 0u : (((e + 896u) << 20) | ((u >> 3) & 0xfffffu));
+        return __hiloint2double(int((u & 0x80000000u) | mag), zero ? 0 : int(u << 29));
+    }
+    return double(v);
+}
+
+// FP32 state: the same sums and maxima as the generic kernel below, with the
+// FP64 pipe doing only what needs FP64: the squares accumulate by FMA into the
+// row sum (exact FP32 values, FP64 products), the divergence is formed in FP64
+// as (q3(x+1) - q3(x-1)) + (q4(y+1) - q4(y-1)) with the factors 1/2 and 1/4
+// applied to the reduced max and sum (exact scalings), and the site norms |B|^2
+// are screened in FP32: a site's FP64 norm is computed only when its FP32 norm
+// (relative error below 2^-22) reaches the running maximum lowered by 2^-20,
+// so no site whose FP64 norm exceeds the maximum is skipped. max |div| is kept
+// as the bit pattern of a non-negative double (integer order = numeric order;
+// NaN excluded, as fmax would).
+__global__ void __launch_bounds__(DIAG_THREADS) diag_partial_f32(const float *__restrict__ q, int Nx, int Ny,
+                                                                 Partial *__restrict__ part) {
+    const size_t P = size_t(Nx) * size_t(Ny);
+    const float *q3 = q + 3 * P, *q4 = q + 4 * P;
+    CSum e{0.0, 0.0}, d{0.0, 0.0};
+    unsigned long long dmax_bits = 0;
+    double b2max = 0.0;
+    float b2thr = 0.0f;
+    unsigned long long nf = 0;
+    for (int y = blockIdx.x; y < Ny; y += gridDim.x) {
+        const int yp = y + 1 == Ny ? 0 : y + 1, ym = y == 0 ? Ny - 1 : y - 1;
+        const size_t r = size_t(y) * Nx;
+        double erow = 0.0, drow = 0.0;
+        for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
+            const size_t i = r + x;
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                v[c] = q[size_t(c) * P + i];
+                if (!isfinite(v[c])) ++nf;
+                const double dv = f2d_exact(v[c]);
+                erow = fma(dv, dv, erow);
+            }
+            const float b2f = fmaf(v[3], v[3], fmaf(v[4], v[4], v[5] * v[5]));
+            if (!(b2f < b2thr)) {  // candidate for the maximum (also when b2f is inf or NaN)
+                const double d3 = f2d_exact(v[3]), d4 = f2d_exact(v[4]), d5 = f2d_exact(v[5]);
+                const double b2 = (d3 * d3 + d4 * d4) + d5 * d5;
+                if (b2 > b2max) {
+                    b2max = b2;
+                    b2thr = __double2float_rd(b2 * (1.0 - 0x1p-20));
+                }
+            }
+            const int xp = x + 1 == Nx ? 0 : x + 1, xm = x == 0 ? Nx - 1 : x - 1;
+            const double dv = (f2d_exact(q3[r + xp]) - f2d_exact(q3[r + xm])) +
+                              (f2d_exact(q4[size_t(yp) * Nx + x]) - f2d_exact(q4[size_t(ym) * Nx + x]));
+            drow = fma(dv, dv, drow);
+            const unsigned long long ab = static_cast<unsigned long long>(__double_as_longlong(dv)) &
+                                          0x7fffffffffffffffull;
+            if (ab <= 0x7ff0000000000000ull && ab > dmax_bits) dmax_bits = ab;
+        }
+        e.add(erow);
+        d.add(0.25 * drow);
+    }
+    const double dmax = 0.5 * __longlong_as_double(static_cast<long long>(dmax_bits));
+    block_reduce_write(Partial{e.s, e.c, d.s, d.c, dmax, sqrt(b2max), nf, 0ull}, part);
+}
+
 // Divergence of D (Sec. 4.2): D = (n_x q0, n_y q1, n_z q2) for the diagonal
 // dielectric eps_i = n_i^2 (Eq. 15: q_i = n_i E_i), central differences in
 // lattice units; the same partition and trees as diag_partial. The record's
@@ -202,7 +274,7 @@ cudaError_t launch_diagnostics(const void *q, int precision, int Nx, int Ny, voi
     const int G = diag_blocks(Nx, Ny);
     Partial *part = static_cast<Partial *>(scratch);
     if (precision == 0)
-        diag_partial<float><<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, part);
+        diag_partial_f32<<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, part);
     else
         diag_partial<double><<<G, DIAG_THREADS, 0, st>>>(static_cast<const double *>(q), Nx, Ny, part);
     cudaError_t e = cudaGetLastError();
@@ -293,7 +365,7 @@ extern "C" qla_status qla_diagnostics_noalloc(const void *q, int precision, int 
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (precision == QLA_FP32)
-        diag_partial<float><<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, s->part);
+        diag_partial_f32<<<G, DIAG_THREADS, 0, st>>>(static_cast<const float *>(q), Nx, Ny, s->part);
     else
         diag_partial<double><<<G, DIAG_THREADS, 0, st>>>(static_cast<const double *>(q), Nx, Ny, s->part);
     if (cudaGetLastError() != cudaSuccess) return QLA_ECUDA;
