@@ -581,10 +581,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
             else tma_planes(true, 2, 1, it, Fm::VX, &tbar[1]);         // V_X (Eq. 23)
         }
     };
-    // bounded wait for a copy group; a timeout sets the error flag (the
-    // results of the launch are then invalid) instead of hanging
+    // bounded wait for a copy group (the warp sleeps until the copies land; at
+    // most 2 s): a timeout sets the error flag (the results of the launch are
+    // then invalid) instead of hanging
     auto tma_wait = [&](int b, uint32_t ph) {
-        if (!tc::mbar_wait(&tbar[b], ph, 1u << 24) && A.error) atomicExch(A.error, 1);
+        if (!tc::mbar_wait_suspended(&tbar[b], ph, 1000000u, 2000000000ull) && A.error) atomicExch(A.error, 1);
     };
 
     for (int i = tid; i < int(L::STATE / sizeof(T)); i += NT) buf[i] = T(0);

@@ -68,6 +68,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
+// Wait on an mbarrier phase with the warp suspended in hardware between tries
+// (suspend-time hint of `suspend_ns`; the warp resumes as soon as the phase
+// completes), so that waiting warps do not take issue slots from working ones.
+// Bounded by the global timer: returns false once `limit_ns` have passed
+// since the first unsuccessful try, whatever the hardware's suspend time.
+__device__ __forceinline__ bool mbar_wait_suspended(uint64_t *bar, uint32_t parity, uint32_t suspend_ns,
+                                                    uint64_t limit_ns) {
+    const uint32_t a = smem_addr(bar);
+    uint64_t t0 = 0;
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity), "r"(suspend_ns)
+            : "memory");
+        if (done) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > limit_ns) return false;
+    }
+}
+
 // Allocate ncols TMEM columns (power of two >= 32); whole warp; the address is
 // written to *dst (shared memory).
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
