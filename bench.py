@@ -30,11 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes per sweep launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-# profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
-# excluded), the workload, steps per pass and rows per tile match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "59088c96c7c8ea6b", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 2, "chunk_rows": 216, "bytes_per_launch": 6.142e9 + 1.593e9}
+# DRAM bytes per sweep launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
+# the same kernel configuration on the 4096^2 version of the workload, scaled by 4 (the traffic of a
+# pass grows with the sites; profiles/sweep_kernel_cylinders8192_launches.md), valid while the
+# sweep's code (comment lines excluded), the workload, steps per pass and rows per tile match.
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "a4de286292ddbd32", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 2, "chunk_rows": 192, "bytes_per_launch": 4 * 1.9409e9}
 
 L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"
@@ -441,7 +442,10 @@ def surrogate_report(calls: int = 250, seed: int = 7):
     except (OSError, ValueError):
         pass
     bf16 = peaks.get("bf16_tflops") or 1900.0
-    achieved = flops / r["forward_seconds_per_call"] / 1e12
+    # algorithmic MACs per site of the network (first layer 9 x 9 x 64 with its 9 input channels,
+    # four hidden 9 x 64 x 64, last 9 x 64 x 6); the kernels compute padded channels (16 in, 16 out)
+    alg_flops = 2 * (9 * 9 * 64 + 4 * 9 * 64 * 64 + 9 * 64 * 6) * w.Nx * w.Ny
+    achieved = alg_flops / r["forward_seconds_per_call"] / 1e12
     curve = [(c["steps"], round(c["rel_l2"], 5)) for c in r["curve"][4::5]]
     variants = []
     if os.path.exists(SURROGATE_CHECKPOINT_K32):
@@ -480,7 +484,9 @@ def surrogate_report(calls: int = 250, seed: int = 7):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                      "frac": achieved / bf16, "peak_kind": "measured" if peaks.get("bf16_tflops") else "fallback",
                      "kernel": "conv3x3_tc_kernel (6 layers, one forward call)",
-                     "flops": "2 x padded MACs: 9 x (16x64 + 4 x 64x64 + 64x16) per site"},
+                     "flops": "2 x algorithmic MACs: 9 x (9x64 + 4 x 64x64 + 64x6) = 156096 per site",
+                     "achieved_padded": flops / r["forward_seconds_per_call"] / 1e12,
+                     "flops_padded": "2 x padded MACs: 9 x (16x64 + 4 x 64x64 + 64x16) per site"},
     }
 
 
@@ -550,8 +556,9 @@ def run_surrogate(args):
     except (OSError, ValueError):
         pass
     bf16 = peaks.get("bf16_tflops") or 1900.0
-    achieved = flops / (fwd_ms / 1e3) / 1e12
     sites = w.Nx * w.Ny
+    alg_flops = 2 * (9 * 9 * 64 + 4 * 9 * 64 * 64 + 9 * 64 * 6) * sites  # algorithmic MACs (see surrogate_report)
+    achieved = alg_flops / (fwd_ms / 1e3) / 1e12
     line = {"metric": "QLA-equivalent site-updates/s of the surrogate forward", "value": sites * 16 / (fwd_ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
@@ -560,6 +567,8 @@ def run_surrogate(args):
             "training_step_ms": train_ms, "training_batch": "4 x 512x256",
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                          "frac": achieved / bf16, "kernel": "conv3x3_tc_kernel (6 layers per call)",
+                         "flops": "2 x algorithmic MACs (156096 per site)",
+                         "achieved_padded": flops / (fwd_ms / 1e3) / 1e12,
                          "peak_kind": "measured" if peaks.get("bf16_tflops") else "fallback"}}
     print(json.dumps(line), flush=True)
 
