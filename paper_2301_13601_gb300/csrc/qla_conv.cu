@@ -332,8 +332,38 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
             const long long o_seg = o;
             __syncwarp();
             if (lane == 0 && int((o_seg - 1) & 1) == grp) mbar_arrive(&empty_bar[g % NS]);  // first halo row
+            // q update (the surrogate's last layer, NOUT = 16): the FP32 input
+            // state of this group's rows is loaded one of its rows ahead, before
+            // the wait for the row's accumulator, so that the load latency overlaps
+            // the wait and the previous row's epilogue (issued after the wait it was
+            // exposed once per row). Other widths load it after the wait.
+            constexpr bool QPRE = NOUT == 16;
+            constexpr int NQ = QPRE ? 6 : 1;
+            const size_t qP = (size_t)H * W;
+            bool qup = false;
+            const float *qi = nullptr;
+            float qv[NQ];
+            auto qload = [&](int i, float (&dst)[NQ]) {
+                const size_t pix = (size_t)(sg.y_s + i) * W + sg.x0 + m;
+#pragma unroll
+                for (int c = 0; c < NQ; ++c) dst[c] = qi[c * qP + pix];
+            };
+            if constexpr (QPRE) {
+                qup = a.epi == EPI_QUPDATE;
+                if (qup) {
+                    qi = static_cast<const float *>(a.aux0) + (size_t)sg.img * 6 * qP;
+                    const int i_first = int(((long long)grp - o_seg) & 1);  // first i with (o_seg + i) mod 2 == grp
+                    if (i_first < sg.len) qload(i_first, qv);
+                }
+            }
             for (int i = 0; i < sg.len; ++i, ++o) {
                 if (int(o & 1) != grp) continue;
+                float qn[NQ];
+                bool q_more = false;
+                if constexpr (QPRE) {
+                    q_more = qup && i + 2 < sg.len;
+                    if (q_more) qload(i + 2, qn);
+                }
                 const int b = int((NB - o % NB) % NB);
                 if (!tc::mbar_wait(&accf_bar[b], uint32_t((o / NB) & 1), CONV_WAIT_TRIES)) {
                     ok = false;
@@ -431,13 +461,21 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
                         store_half_bf16<NC, NOUT, L::STG_STRIDE>(stg, dzv, static_cast<__nv_bfloat16 *>(a.out1),
                                                                  p - lane, cb0, lane);
                     } else if (cb0 == 0) {  // EPI_QUPDATE: channels 0..5
-                        const size_t P = (size_t)H * W;
                         const size_t pix = (size_t)y * W + sg.x0 + m;
-                        const float *qi = static_cast<const float *>(a.aux0) + (size_t)sg.img * 6 * P;
-                        float *qo = static_cast<float *>(a.out0) + (size_t)sg.img * 6 * P;
+                        float *qo = static_cast<float *>(a.out0) + (size_t)sg.img * 6 * qP;
+                        if constexpr (QPRE) {
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) qo[c * P + pix] = qi[c * P + pix] + a.scale * v[c];
+                            for (int c = 0; c < 6; ++c) qo[c * qP + pix] = qv[c] + a.scale * v[c];
+                        } else {
+                            const float *qin = static_cast<const float *>(a.aux0) + (size_t)sg.img * 6 * qP;
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) qo[c * qP + pix] = qin[c * qP + pix] + a.scale * v[c];
+                        }
                     }
+                }
+                if (q_more) {
+#pragma unroll
+                    for (int c = 0; c < NQ; ++c) qv[c] = qn[c];
                 }
                 tc::fence_before_sync();
                 __syncwarp();
