@@ -126,8 +126,10 @@ __device__ __forceinline__ double f2d_exact(float v) {
 }
 
 // FP32 state: the same sums and maxima as the generic kernel below, with the
-// FP64 pipe doing only what needs FP64: the squares accumulate by FMA into the
-// row sum (exact FP32 values, FP64 products), the divergence is formed in FP64
+// FP64 pipe doing only what needs FP64: a site's squares are summed as an
+// exact-product float pair and enter the FP64 row sum by two additions (sites
+// with values beyond 2^+-60, where FP32 squares could overflow or lose their
+// error term, take FP64 squares instead), the divergence is formed in FP64
 // as (q3(x+1) - q3(x-1)) + (q4(y+1) - q4(y-1)) with the factors 1/2 and 1/4
 // applied to the reduced max and sum (exact scalings), and the site norms |B|^2
 // are screened in FP32: a site's FP64 norm is computed only when its FP32 norm
@@ -151,12 +153,38 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_f32(const float *__
         for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
             const size_t i = r + x;
             float v[6];
+            bool ff = true;  // every |v| zero or in [2^-60, 2^60): FP32 squares and their errors are exact
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 v[c] = q[size_t(c) * P + i];
                 if (!isfinite(v[c])) ++nf;
-                const double dv = f2d_exact(v[c]);
-                erow = fma(dv, dv, erow);
+                const unsigned ua = __float_as_uint(v[c]) & 0x7fffffffu;
+                ff = ff && (ua == 0u || ua - 0x21800000u < 0x3c000000u);
+            }
+            if (ff) {
+                // the site's sum of squares as an unevaluated float pair: each
+                // square is p + e exactly (e by FMA), the p are added by TwoSum,
+                // the low parts in FP32 (relative error ~2^-47 of the site value,
+                // unbiased); two FP64 additions enter it into the row sum
+                // (intrinsics: no contraction of a product into the TwoSum)
+                float hi = __fmul_rn(v[0], v[0]), lo = __fmaf_rn(v[0], v[0], -hi);
+#pragma unroll
+                for (int c = 1; c < 6; ++c) {
+                    const float pc = __fmul_rn(v[c], v[c]);
+                    const float ec = __fmaf_rn(v[c], v[c], -pc);
+                    const float sc = __fadd_rn(hi, pc);
+                    const float bb = __fsub_rn(sc, hi);
+                    const float tc = __fadd_rn(__fsub_rn(hi, __fsub_rn(sc, bb)), __fsub_rn(pc, bb));
+                    lo = __fadd_rn(lo, __fadd_rn(tc, ec));
+                    hi = sc;
+                }
+                erow = (erow + f2d_exact(hi)) + f2d_exact(lo);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const double dv = f2d_exact(v[c]);
+                    erow = fma(dv, dv, erow);
+                }
             }
             const float b2f = fmaf(v[3], v[3], fmaf(v[4], v[4], v[5] * v[5]));
             if (!(b2f < b2thr)) {  // candidate for the maximum (also when b2f is inf or NaN)

@@ -168,6 +168,32 @@ def test_diagnostics_match_oracle(precision):
     assert abs(d["b_max"] - b) <= 1e-14 * b
 
 
+@pytest.mark.parametrize("scale", [1e-30, 1e25, "mixed"])
+def test_diagnostics_extreme_values_fp32(scale):
+    """FP32 states whose values leave [2^-60, 2^60) (where FP32 squares would
+    underflow or overflow) are reduced with FP64 squares: the energy and the
+    other statistics still agree with the oracle."""
+    Nx, Ny = 300, 77
+    rng = np.random.default_rng(15)
+    q = rng.standard_normal((6, Ny, Nx))
+    if scale == "mixed":
+        q[:, ::7, ::5] *= 1e22
+        q[:, 1::9, ::3] *= 1e-24
+    else:
+        q *= scale
+    q = q.astype(np.float32).astype(np.float64)
+    n = media.uniform_medium(Nx, Ny, (1.2, 1.3, 1.4))
+    with Simulation(*n, 0.1, precision="fp32") as sim:
+        sim.set_fields(q)
+        d = sim.diagnostics()
+    assert d["nonfinite"] == 0
+    assert abs(d["energy"] - oracle.energy(q)) <= 1e-14 * oracle.energy(q)
+    s, m, b = oracle.divB(q)
+    assert abs(d["div_l2_sq"] - s) <= 1e-13 * s
+    assert abs(d["div_max"] - m) <= 1e-14 * m
+    assert abs(d["b_max"] - b) <= 1e-14 * b
+
+
 def test_diagnostics_deterministic():
     Nx, Ny = 1000, 700
     q = np.random.default_rng(9).standard_normal((6, Ny, Nx))
