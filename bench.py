@@ -458,7 +458,8 @@ def surrogate_report(calls: int = 250, seed: int = 7):
             "K": m32["K"], "checkpoint": os.path.relpath(SURROGATE_CHECKPOINT_K32, ROOT),
             "trained": {k: m32[k] for k in ("trajectories", "iters", "noise", "final_loss", "train_seconds")},
             "rel_l2": r32["rel_l2"], "horizon_steps_rel_l2_1e-2": r32["horizon_steps_rel_l2_1e-2"],
-            "speedup_at_rel_l2_1e-2": r32["speedup_at_rel_l2_1e-2"], "speedup_rollout": r32["speedup_rollout"],
+            "speedup_at_rel_l2_1e-2": r32["speedup_at_rel_l2_1e-2"],
+            "speedup_at_rel_l2_1e-2_serial": r32["speedup_at_rel_l2_1e-2_serial"], "speedup_rollout": r32["speedup_rollout"],
             "speedup_forward": r32["speedup_forward"], "surrogate_calls": r32["surrogate_calls"],
             "fallback_calls": r32["fallback_calls"]})
     return {
@@ -469,6 +470,7 @@ def surrogate_report(calls: int = 250, seed: int = 7):
         "rel_l2": r["rel_l2"], "rel_l2_no_update": r["rel_l2_no_update"],
         "horizon_steps_rel_l2_1e-2": r["horizon_steps_rel_l2_1e-2"],
         "speedup_at_rel_l2_1e-2": r["speedup_at_rel_l2_1e-2"],
+        "speedup_at_rel_l2_1e-2_serial": r["speedup_at_rel_l2_1e-2_serial"],
         "speedup_rollout": r["speedup_rollout"], "speedup_forward": r["speedup_forward"],
         "surrogate_calls": r["surrogate_calls"], "fallback_calls": r["fallback_calls"],
         "energy_drift": r["energy_drift"], "qla_energy_drift": r["qla_energy_drift"],

@@ -126,8 +126,9 @@ qla_status qla_surrogate_synchronize(qla_surrogate *s);
 
 /* Energy checks of qla_surrogate_rollout. */
 enum {
-    QLA_DRIFT_PER_CALL = 0,   /* |E(proposal) / E(state the call starts from) - 1| */
-    QLA_DRIFT_FROM_START = 1  /* |E(proposal) / E_ref - 1|, E_ref fixed for the whole rollout */
+    QLA_DRIFT_PER_CALL = 0,    /* |E(proposal) / E(state the call starts from) - 1| */
+    QLA_DRIFT_FROM_START = 1,  /* |E(proposal) / E_ref - 1|, E_ref fixed for the whole rollout */
+    QLA_ROLLOUT_SERIAL = 16    /* flag (OR into drift_mode): no speculative next call (see below) */
 };
 
 /* Advance an FP32 QLA context by `calls` x K steps with the network. After each
@@ -141,7 +142,14 @@ enum {
  * n: device FP32 [3][Ny][Nx]. The surrogate must have nimg == 1 and the
  * context's lattice, and the context must advance both polarisation families
  * (QLA_EUNSUPPORTED otherwise: the network writes all six components). Runs
- * on the context's stream; synchronous. */
+ * on the context's stream; synchronous.
+ * Speculation: while the host reads a call's energy, the next call's network
+ * pass is already running on the proposal (in a third state buffer the
+ * surrogate holds), so the GPU does not wait for the host between accepted
+ * calls; after a rejection the speculative pass is discarded. The states,
+ * decisions and statistics are those of the serial loop, which
+ * QLA_ROLLOUT_SERIAL in drift_mode selects (tests compare the two bit for
+ * bit). */
 qla_status qla_surrogate_rollout(qla_surrogate *s, qla_ctx *ctx, const float *n, int calls, double drift_tol,
                                  int drift_mode, double energy_ref, qla_rollout_stats *stats);
 

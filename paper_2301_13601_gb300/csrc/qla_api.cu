@@ -586,4 +586,6 @@ void ctx_commit_spare(qla_ctx *c, long long steps) {
     c->steps += steps;
 }
 
+void ctx_add_steps(qla_ctx *c, long long steps) { c->steps += steps; }
+
 }  // namespace qla

@@ -160,5 +160,7 @@ struct CtxView {
 bool ctx_view(qla_ctx *c, CtxView *v);
 // The spare buffer, now holding the state `steps` steps later, becomes current.
 void ctx_commit_spare(qla_ctx *c, long long steps);
+// The current buffer was advanced in place by `steps` steps (step count only).
+void ctx_add_steps(qla_ctx *c, long long steps);
 }  // namespace qla
 

@@ -246,8 +246,10 @@ struct qla_surrogate {
     float *wpart = nullptr, *bpart = nullptr;
     double *red = nullptr, *scal = nullptr;  // scal[0] = sum dQ^2, scal[1] = sum residual^2
     int *err = nullptr;
-    double *host_scal = nullptr;  // pinned [2]
+    double *host_scal = nullptr;  // pinned [4]: loss sums, rollout energies (two slots)
     int *host_err = nullptr;      // pinned
+    float *qspec = nullptr;       // third state buffer of a one-image surrogate (speculative rollout calls)
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // rollout: a call's energy has reached the host
     bool packed = false;
     long long adam_t = 0;
     qla_status sticky = QLA_OK;
@@ -503,6 +505,7 @@ qla_status qla_surrogate_create(const qla_surrogate_config *cfg, qla_surrogate *
     add(RED_BLOCKS * 8);                                                                         // red
     add(4 * 8);                                                                                  // scal
     add(sizeof(int));                                                                            // err
+    add(c.nimg == 1 ? size_t(6) * size_t(s->P) * 4 : 0);                                         // qspec
     size_t total = 0;
     for (size_t b : sizes) total += b;
     if (cudaMalloc(&s->arena, total) != cudaSuccess) {
@@ -536,8 +539,11 @@ qla_status qla_surrogate_create(const qla_surrogate_config *cfg, qla_surrogate *
     s->red = static_cast<double *>(take());
     s->scal = static_cast<double *>(take());
     s->err = static_cast<int *>(take());
+    s->qspec = static_cast<float *>(take());
     if (cudaMallocHost(&s->host_scal, 4 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&s->host_err, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&s->host_err, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         qla_surrogate_destroy(s);
         return QLA_ENOMEM;
@@ -654,8 +660,10 @@ qla_status qla_surrogate_rollout(qla_surrogate *s, qla_ctx *ctx, const float *n,
     qla_status r = enter(s);
     if (r != QLA_OK) return r;
     CtxView v;
+    const bool serial = (drift_mode & QLA_ROLLOUT_SERIAL) != 0;
+    const int mode = drift_mode & ~QLA_ROLLOUT_SERIAL;
     if (!ctx || !n || calls < 0 || !(drift_tol >= 0.0) || !ctx_view(ctx, &v) ||
-        (drift_mode != QLA_DRIFT_PER_CALL && drift_mode != QLA_DRIFT_FROM_START))
+        (mode != QLA_DRIFT_PER_CALL && mode != QLA_DRIFT_FROM_START))
         return sfail(s, QLA_EINVAL, "rollout: bad argument");
     if (v.precision != QLA_FP32) return sfail(s, QLA_EUNSUPPORTED, "rollout: the context must be FP32");
     if (v.families != QLA_FAMILIES_BOTH)  // the network writes all six components
@@ -669,59 +677,152 @@ qla_status qla_surrogate_rollout(qla_surrogate *s, qla_ctx *ctx, const float *n,
         r = repack(s, v.stream);
         if (r != QLA_OK) return r;
     }
-    // Eq. 27 energy (mean over sites of Q.Q) of a proposal or state: one light
-    // reduction (the full diagnostics add div B and compensated FP64 sums,
-    // which the drift check does not need and which cost more than the check).
-    auto energy = [&](const void *q, double *e, bool *finite) -> qla_status {
-        sumsq_kernel<<<RED_BLOCKS, 256, 0, v.stream>>>(static_cast<const float *>(q), 6LL * v.Nx * v.Ny, s->red);
-        finalize_kernel<<<1, 256, 0, v.stream>>>(s->red, RED_BLOCKS, s->scal + 2);
+    const cudaStream_t st = v.stream;
+    const double sites = double(v.Nx) * v.Ny;
+    // Eq. 27 energy (mean over sites of Q.Q) of a state: one light reduction
+    // (the full diagnostics add div B and compensated FP64 sums, which the
+    // drift check does not need and which cost more than the check), its
+    // result and the error flag copied to pinned host slot `slot`.
+    auto launch_energy = [&](const void *q, int slot) -> qla_status {
+        sumsq_kernel<<<RED_BLOCKS, 256, 0, st>>>(static_cast<const float *>(q), 6LL * v.Nx * v.Ny, s->red);
+        finalize_kernel<<<1, 256, 0, st>>>(s->red, RED_BLOCKS, s->scal + 2 + slot);
         SG_CUDA(s, cudaGetLastError());
-        SG_CUDA(s, cudaMemcpyAsync(s->host_scal + 2, s->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, v.stream));
-        SG_CUDA(s, cudaMemcpyAsync(s->host_err, s->err, sizeof(int), cudaMemcpyDeviceToHost, v.stream));
-        SG_CUDA(s, cudaStreamSynchronize(v.stream));
+        SG_CUDA(s, cudaMemcpyAsync(s->host_scal + 2 + slot, s->scal + 2 + slot, sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+        SG_CUDA(s, cudaMemcpyAsync(s->host_err, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SG_CUDA(s, cudaEventRecord(s->ev[slot], st));
+        return QLA_OK;
+    };
+    auto read_energy = [&](int slot, double *e, bool *finite) -> qla_status {
+        SG_CUDA(s, cudaEventSynchronize(s->ev[slot]));
         if (*s->host_err) return sfail(s, QLA_ETIMEOUT, "rollout: a tensor-core wait ran out of its limit");
-        *e = s->host_scal[2] / (double(v.Nx) * v.Ny);
+        *e = s->host_scal[2 + slot] / sites;
         *finite = isfinite(*e) != 0;
         return QLA_OK;
     };
-    qla_rollout_stats st{};
+    auto energy = [&](const void *q, double *e, bool *finite) -> qla_status {
+        qla_status rr = launch_energy(q, 0);
+        return rr == QLA_OK ? read_energy(0, e, finite) : rr;
+    };
+    qla_rollout_stats stt{};
     bool fin = true;
     double e_start = 0.0;
     r = energy(v.cur_state, &e_start, &fin);
     if (r != QLA_OK) return r;
     if (!fin || !(e_start > 0.0)) return sfail(s, QLA_ESTATE, "rollout: initial state has no finite energy");
-    st.energy_ref = (drift_mode == QLA_DRIFT_FROM_START && energy_ref > 0.0 && isfinite(energy_ref)) ? energy_ref : e_start;
+    stt.energy_ref = (mode == QLA_DRIFT_FROM_START && energy_ref > 0.0 && isfinite(energy_ref)) ? energy_ref : e_start;
     double e_cur = e_start;  // energy of the current state (reference of the per-call check)
-    for (int k = 0; k < calls; ++k) {
-        ctx_view(ctx, &v);
-        r = forward_infer(s, static_cast<const float *>(v.cur_state), n, static_cast<float *>(v.spare_state), v.stream);
-        if (r != QLA_OK) return r;
-        double e = 0.0;
-        r = energy(v.spare_state, &e, &fin);
-        if (r != QLA_OK) return r;
-        const double ref = drift_mode == QLA_DRIFT_PER_CALL ? e_cur : st.energy_ref;
+    // the decision on one proposal of energy e (updates the statistics)
+    auto accept = [&](double e, bool finite) {
+        const double ref = mode == QLA_DRIFT_PER_CALL ? e_cur : stt.energy_ref;
         const double drift = fabs(e / ref - 1.0);
-        st.calls += 1;
-        if (fin && drift <= drift_tol) {
-            ctx_commit_spare(ctx, s->cfg.K);
-            st.surrogate_calls += 1;
-            if (drift > st.max_drift) st.max_drift = drift;
+        stt.calls += 1;
+        if (finite && drift <= drift_tol) {
+            stt.surrogate_calls += 1;
+            if (drift > stt.max_drift) stt.max_drift = drift;
             e_cur = e;
-        } else {
-            r = qla_step(ctx, s->cfg.K);
-            if (r != QLA_OK) return sfail(s, r, "rollout: fallback qla_step failed: %s", qla_last_error(ctx));
-            st.fallback_calls += 1;
-            if (drift_mode == QLA_DRIFT_PER_CALL) {
-                ctx_view(ctx, &v);
-                r = energy(v.cur_state, &e_cur, &fin);
+            return true;
+        }
+        stt.fallback_calls += 1;
+        return false;
+    };
+    // K plain QLA steps from the context's current state after a rejection
+    auto fallback = [&]() -> qla_status {
+        qla_status rr = qla_step(ctx, s->cfg.K);
+        if (rr != QLA_OK) return sfail(s, rr, "rollout: fallback qla_step failed: %s", qla_last_error(ctx));
+        if (mode == QLA_DRIFT_PER_CALL) {
+            bool f2 = true;
+            ctx_view(ctx, &v);
+            rr = energy(v.cur_state, &e_cur, &f2);
+        }
+        return rr;
+    };
+    if (serial) {
+        for (int k = 0; k < calls; ++k) {
+            ctx_view(ctx, &v);
+            r = forward_infer(s, static_cast<const float *>(v.cur_state), n, static_cast<float *>(v.spare_state), st);
+            if (r != QLA_OK) return r;
+            double e = 0.0;
+            r = energy(v.spare_state, &e, &fin);
+            if (r != QLA_OK) return r;
+            if (accept(e, fin)) {
+                ctx_commit_spare(ctx, s->cfg.K);
+            } else {
+                r = fallback();
                 if (r != QLA_OK) return r;
             }
         }
+    } else {
+        // Three state buffers: the context's two (A, B) and the surrogate's
+        // qspec. `cur` holds the accepted state, `pend` the proposal of the
+        // call being decided, `next` the speculative proposal computed from
+        // `pend`; each is one of the three. The context's own current buffer
+        // is brought up to date (sync_ctx) before a fallback and at the end.
+        float *const A = static_cast<float *>(v.cur_state), *const B = static_cast<float *>(v.spare_state);
+        float *const X = s->qspec;
+        float *cur = A;
+        long long pending_steps = 0;  // accepted steps not yet counted by the context
+        auto free_buf = [&](const float *a, const float *b) { return (A != a && A != b) ? A : (B != a && B != b) ? B : X; };
+        auto sync_ctx = [&]() -> qla_status {
+            ctx_view(ctx, &v);
+            if (cur == v.cur_state) {
+                ctx_add_steps(ctx, pending_steps);
+            } else {
+                if (cur == X)
+                    SG_CUDA(s, cudaMemcpyAsync(v.spare_state, X, sizeof(float) * 6 * size_t(v.Nx) * v.Ny,
+                                               cudaMemcpyDeviceToDevice, st));
+                ctx_commit_spare(ctx, pending_steps);
+            }
+            pending_steps = 0;
+            ctx_view(ctx, &v);
+            cur = static_cast<float *>(v.cur_state);
+            return QLA_OK;
+        };
+        auto launch_call = [&](const float *src, float *dst, int slot) -> qla_status {
+            qla_status rr = forward_infer(s, src, n, dst, st);
+            return rr == QLA_OK ? launch_energy(dst, slot) : rr;
+        };
+        float *pend = nullptr;
+        int slot = 0;
+        for (int k = 0; k < calls; ++k) {
+            if (!pend) {  // (re)start the pipeline from the accepted state
+                pend = free_buf(cur, nullptr);
+                slot = 0;
+                r = launch_call(cur, pend, slot);
+                if (r != QLA_OK) return r;
+            }
+            float *next = nullptr;
+            if (k + 1 < calls) {  // the next call, on the assumption that this one is accepted
+                next = free_buf(cur, pend);
+                r = launch_call(pend, next, slot ^ 1);
+                if (r != QLA_OK) return r;
+            }
+            double e = 0.0;
+            r = read_energy(slot, &e, &fin);
+            if (r != QLA_OK) return r;
+            if (accept(e, fin)) {
+                cur = pend;
+                pending_steps += s->cfg.K;
+                pend = next;
+                slot ^= 1;
+            } else {
+                SG_CUDA(s, cudaStreamSynchronize(st));  // the speculative call is discarded
+                r = sync_ctx();
+                if (r != QLA_OK) return r;
+                r = fallback();
+                if (r != QLA_OK) return r;
+                ctx_view(ctx, &v);
+                cur = static_cast<float *>(v.cur_state);
+                pend = nullptr;
+            }
+        }
+        r = sync_ctx();
+        if (r != QLA_OK) return r;
     }
     ctx_view(ctx, &v);
-    r = energy(v.cur_state, &st.energy_final, &fin);
+    r = energy(v.cur_state, &stt.energy_final, &fin);
     if (r != QLA_OK) return r;
-    if (stats) *stats = st;
+    if (stats) *stats = stt;
     return QLA_OK;
 }
 
@@ -744,6 +845,8 @@ void qla_surrogate_destroy(qla_surrogate *s) {
     if (s->arena) cudaFree(s->arena);
     if (s->host_scal) cudaFreeHost(s->host_scal);
     if (s->host_err) cudaFreeHost(s->host_err);
+    for (cudaEvent_t e : s->ev)
+        if (e) cudaEventDestroy(e);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -12,6 +12,7 @@ from .qla import QLAError, STATUS, load_library
 
 EPI_GELU, EPI_LINEAR, EPI_DGRAD, EPI_QUPDATE = 0, 1, 2, 3
 DRIFT_PER_CALL, DRIFT_FROM_START = 0, 1
+ROLLOUT_SERIAL = 16  # flag: no speculative next call in qla_surrogate_rollout
 
 EXPORTS = ["qla_conv3x3_bf16", "qla_pack_conv_weights"]
 
@@ -230,13 +231,15 @@ class Surrogate:
         self._check(self._L.qla_surrogate_synchronize(self._h), "synchronize")
 
     def rollout(self, sim, n, calls: int, drift_tol: float = 1e-3, drift_mode: int = DRIFT_PER_CALL,
-                energy_ref: float = 0.0) -> dict:
-        """Advance a Simulation (FP32) by calls x K steps; see qla_surrogate_rollout."""
+                energy_ref: float = 0.0, serial: bool = False) -> dict:
+        """Advance a Simulation (FP32) by calls x K steps; see qla_surrogate_rollout
+        (serial=True: no speculative next call)."""
         import torch
 
         torch.cuda.synchronize()
         st = RolloutStats()
-        self._check(self._L.qla_surrogate_rollout(self._h, sim._ctx, _ptr(n), calls, drift_tol, drift_mode,
+        mode = drift_mode | (ROLLOUT_SERIAL if serial else 0)
+        self._check(self._L.qla_surrogate_rollout(self._h, sim._ctx, _ptr(n), calls, drift_tol, mode,
                                                   energy_ref, ctypes.byref(st)), "rollout")
         return {k: getattr(st, k) for k, _ in RolloutStats._fields_}
 

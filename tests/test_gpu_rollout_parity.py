@@ -93,3 +93,38 @@ def test_accept_reject_decision_is_the_oracles(setup):
         sim.step(meta["K"])
         qla = sim.get_fields(dtype=np.float32)
     assert np.array_equal(got, qla)
+
+
+@pytest.mark.parametrize("mode", [S.DRIFT_PER_CALL, S.DRIFT_FROM_START])
+def test_speculative_rollout_equals_the_serial_loop(setup, mode):
+    """The default rollout runs the next call's network pass while the host
+    reads the current call's energy (a third state buffer) and discards it on
+    a rejection; its states, decisions and statistics must be the serial
+    loop's, bit for bit, on a run that mixes accepted and rejected calls."""
+    params, meta, n, nf, q, prop, e_start, e_prop = setup
+    calls = 12
+
+    def run(tol, serial):
+        with Simulation(*n, DELTA, precision="fp32") as sim, \
+                S.Surrogate(H, W, K=meta["K"], out_scale=meta["out_scale"]) as sur:
+            sur.set_params(params)
+            sim.set_fields(q)
+            st = sur.rollout(sim, nf, calls, drift_tol=tol, drift_mode=mode, serial=serial)
+            return st, sim.get_fields(dtype=np.float32), sim.step_count
+
+    chosen = None
+    for tol in np.geomspace(1e-4, 3e-2, 25):  # the network's drift per call is ~1e-2 on this state
+        st, got, steps = run(tol, True)
+        if 0 < st["fallback_calls"] < calls:
+            chosen = (float(tol), st, got, steps)
+            break
+    assert chosen, "no tolerance gives a mix of accepted and rejected calls"
+    tol, st_s, got_s, steps_s = chosen
+    st_p, got_p, steps_p = run(tol, False)
+    print(f"tol {tol}: serial {st_s}, speculative {st_p}")
+    assert steps_p == steps_s == calls * meta["K"]
+    assert st_p == st_s
+    assert np.array_equal(got_p, got_s)
+    for tol in (0.0, 1.0):  # all rejected / all accepted
+        a, b = run(tol, True), run(tol, False)
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
