@@ -43,6 +43,27 @@ qla_status qla_conv3x3_bf16(const void *x, int nimg, int H, int W, int cin, cons
                             int nout, int epilogue, const void *aux0, const void *zprev, void *out0, void *out1,
                             float scale, int *error_flag, void *stream);
 
+/* The MMA issue schedule of one CTA of qla_conv3x3_bf16 (cin, nout as there;
+ * the CTA takes rows [T cta / grid, T (cta + 1) / grid) of the T = nimg H W/128
+ * (image, column block, row) items), enumerated on the host by the same code
+ * the kernel's MMA warp runs; for tests. No GPU is touched. Each record is
+ * QLA_CONV_SCHEDULE_FIELDS ints [type, r, on, j, len, a, b, c, d, e, f, g, h, 0]
+ * with r the ring row, on the output row fed by y tap 0, j the input row of
+ * the run of len output rows, and per type:
+ *   0 MMA: a = x tap, b = 16-channel slice, c..d = y taps ka..kb, e = first
+ *     accumulator block, f = accumulate flag, g = A start and h = B start
+ *     (16-byte units from the ring slot and the packed weights);
+ *   1 accumulator of output row on - 2 complete: a = its block;
+ *   2 wait for the epilogue of the block's previous row before the row's MMAs:
+ *     a = block, b = phase parity;
+ *   3 the row's ring slot released by the tensor cores: a = slot.
+ * At most `capacity` records are written to `records` (host); *count gets the
+ * total. Errors: QLA_EINVAL (sizes, W not a multiple of 128, cta out of range,
+ * NULL count), QLA_EUNSUPPORTED (channel pair). */
+#define QLA_CONV_SCHEDULE_FIELDS 14
+qla_status qla_conv_schedule(int cin, int nout, int nimg, int H, int W, int grid, int cta, int *records,
+                             long long capacity, long long *count);
+
 /* Pack FP32 weights w[nout][cin][3][3] (device) into the BF16 B-operand layout
  * [9][cin_pad/8][nout_pad][8], zero-padded. transpose_flip != 0 packs the
  * adjoint (input-gradient) convolution instead, w'[c][n][ky][kx] =

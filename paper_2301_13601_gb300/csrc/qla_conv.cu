@@ -128,7 +128,7 @@ __device__ __forceinline__ void store_half_bf16(uint8_t *stg, const uint4 (&vals
 struct ConvSeg {
     int img, x0, y_s, len;
 };
-__device__ __forceinline__ ConvSeg conv_segment(long long u0, long long u_end, int H, int TPR) {
+__host__ __device__ __forceinline__ ConvSeg conv_segment(long long u0, long long u_end, int H, int TPR) {
     ConvSeg g;
     g.y_s = int(u0 % H);
     const long long t2 = u0 / H;
@@ -137,6 +137,82 @@ __device__ __forceinline__ ConvSeg conv_segment(long long u0, long long u_end, i
     const long long end = (u0 - g.y_s + H) < u_end ? (u0 - g.y_s + H) : u_end;
     g.len = int(end - u0);
     return g;
+}
+
+// ---------------------------------------------------------------------------
+// The MMA issue schedule, shared by the kernel's MMA warp and by the host-side
+// enumeration (qla_conv_schedule) that tests/test_conv_schedule.py checks.
+// Input row j of a run of `len` output rows (ring row r) feeds output rows
+// j - ky (ky = 0..2); output row `on` = o_run + j owns accumulator block
+// b0 = (-on) mod NB of the TMEM ring, so the rows it feeds are consecutive
+// blocks and one MMA covers them (split in two where the ring wraps).
+// ---------------------------------------------------------------------------
+struct ConvMma {
+    int kx, k2;      // x tap, 16-channel slice
+    int ka, kb;      // y taps ka..kb in one MMA (N = (kb - ka + 1) NOUT)
+    int blk;         // accumulator block of y tap ka
+    int acc;         // 0: the first MMA of a new accumulator (accumulation off)
+    uint32_t a_off;  // A descriptor start, 16-byte units from the row's ring slot
+    uint32_t b_off;  // B descriptor start, 16-byte units from the weights
+};
+
+__host__ __device__ __forceinline__ int conv_block(long long on, int NB) { return int((NB - on % NB) % NB); }
+
+// The MMAs of input row j: the y taps whose output row lies inside the run,
+// split where the block ring wraps, the first MMA of a new accumulator (x tap
+// 0, first slice, ky = 0) alone with accumulation off.
+template <int CCH, int NOUT, int NS, int HP, class F>
+__host__ __device__ __forceinline__ void conv_row_mmas(int j, int len, int b0, F &&emit) {
+    constexpr int NB = 512 / NOUT;
+    const int k_lo = j - len + 1 > 0 ? j - len + 1 : 0;
+    const int k_hi = j < 2 ? j : 2;
+    const int wrap = NB - b0;  // first ky whose block wraps to 0
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+        for (int k2 = 0; k2 < CCH / 2; ++k2) {
+            const bool first = kx == 0 && k2 == 0;
+            for (int ka = k_lo; ka <= k_hi;) {
+                int kb = k_hi;
+                if (ka < wrap && wrap <= kb) kb = wrap - 1;
+                if (first && ka == 0) kb = 0;
+                const int blk = b0 + ka < NB ? b0 + ka : b0 + ka - NB;
+                emit(ConvMma{kx, k2, ka, kb, blk, (first && ka == 0) ? 0 : 1, uint32_t((2 * k2) * NS * HP + kx),
+                             uint32_t((kx * CCH + 2 * k2) * 3 * NOUT + ka * NOUT)});
+                ka = kb + 1;
+            }
+        }
+    }
+}
+
+// Before the MMAs of input row j: a new accumulator (j < len) reuses the block
+// of output row on - NB, so the MMA warp waits for that row's epilogue on
+// acc_empty[b0], phase parity (on / NB + 1) & 1. Returns false if no wait.
+__host__ __device__ __forceinline__ bool conv_row_acc_wait(int j, int len, long long on, int NB, uint32_t *parity) {
+    *parity = uint32_t(((on / NB) + 1) & 1);
+    return j < len && on >= NB;
+}
+
+// After the MMAs of input row j: output row on - 2 has all its taps; its
+// block is committed to acc_full (-1: none yet).
+__host__ __device__ __forceinline__ int conv_row_done_block(int j, long long on, int NB) {
+    return j >= 2 ? conv_block(on - 2, NB) : -1;
+}
+
+// Walks the CTA's rows in the order of every role: for each run, input rows
+// j = 0 .. len + 1 (ring row g + j, output row o + j); row(sg, j, r, on)
+// returns false to stop.
+template <class F>
+__host__ __device__ __forceinline__ void conv_walk_rows(long long u_begin, long long u_end, int H, int TPR, F &&row) {
+    long long g = 0, o = 0;
+    for (long long u0 = u_begin; u0 < u_end;) {
+        const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
+        for (int j = 0; j < sg.len + 2; ++j)
+            if (!row(sg, j, g + j, o + j)) return;
+        g += sg.len + 2;
+        o += sg.len;
+        u0 += sg.len;
+    }
 }
 
 // Persistent, warp-specialised conv kernel (320 threads = 10 warps). Work =
@@ -257,54 +333,29 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3x3_tc_kernel(const ConvA
         const uint64_t bd0 = tc::make_desc(tc::smem_addr(Bs), B_LBO, B_SBO);
         const uint32_t a_lo0 = uint32_t(ad0), a_hi = uint32_t(ad0 >> 32);
         const uint32_t b_lo0 = uint32_t(bd0), b_hi = uint32_t(bd0 >> 32);
-        long long g = 0, o = 0;
         bool ok = true;
-        for (long long u0 = u_begin; u0 < u_end && ok;) {
-            const ConvSeg sg = conv_segment(u0, u_end, H, TPR);
-            for (int j = 0; j < sg.len + 2 && ok; ++j) {
-                const long long r = g + j;   // ring row
-                const long long on = o + j;  // output row whose y tap 0 is this row
-                const int b0 = int((NB - on % NB) % NB);
-                if (!tc::mbar_wait(&full_bar[r % NS], uint32_t((r / NS) & 1), CONV_WAIT_TRIES)) ok = false;
-                // a new accumulator reuses the block of output row on - NB
-                if (ok && j < sg.len && on >= NB &&
-                    !tc::mbar_wait(&acce_bar[b0], uint32_t(((on / NB) + 1) & 1), CONV_WAIT_TRIES))
-                    ok = false;
-                if (!ok) break;
-                tc::fence_after_sync();
-                if (lane == 0) {
-                    const int k_lo = j - sg.len + 1 > 0 ? j - sg.len + 1 : 0;  // y taps whose output row
-                    const int k_hi = j < 2 ? j : 2;                          // lies inside the run
-                    const int wrap = NB - b0;  // first ky whose block wraps to 0
-                    const uint32_t a_row = a_lo0 + uint32_t(int(r % NS) * HP);  // (slot * HP * 16) >> 4
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
-#pragma unroll
-                        for (int k2 = 0; k2 < CCH / 2; ++k2) {
-                            const bool first = kx == 0 && k2 == 0;
-                            const uint32_t a_lo = a_row + uint32_t((2 * k2) * NS * HP + kx);
-                            const uint32_t b_lo = b_lo0 + uint32_t((kx * CCH + 2 * k2) * 3 * NOUT);
-                            for (int ka = k_lo; ka <= k_hi;) {
-                                int kb = k_hi;
-                                if (ka < wrap && wrap <= kb) kb = wrap - 1;
-                                if (first && ka == 0) kb = 0;
-                                const int blk = b0 + ka < NB ? b0 + ka : b0 + ka - NB;
-                                const uint32_t idesc = kb == ka ? IDESC1 : (kb == ka + 1 ? IDESC2 : IDESC3);
-                                tc::mma_bf16_lohi(tmem + uint32_t(blk * NOUT), a_lo, a_hi, b_lo + uint32_t(ka * NOUT),
-                                                  b_hi, idesc, (first && ka == 0) ? 0u : 1u);
-                                ka = kb + 1;
-                            }
-                        }
-                    }
-                    tc::mma_commit(&empty_bar[r % NS]);  // the tensor cores are done with row r
-                    if (j >= 2) tc::mma_commit(&accf_bar[int((NB - (on - 2) % NB) % NB)]);  // output row on - 2
-                }
-                __syncwarp();
+        conv_walk_rows(u_begin, u_end, H, TPR, [&](const ConvSeg &sg, int j, long long r, long long on) {
+            const int b0 = conv_block(on, NB);
+            if (!tc::mbar_wait(&full_bar[r % NS], uint32_t((r / NS) & 1), CONV_WAIT_TRIES)) ok = false;
+            uint32_t par = 0;
+            if (ok && conv_row_acc_wait(j, sg.len, on, NB, &par) && !tc::mbar_wait(&acce_bar[b0], par, CONV_WAIT_TRIES))
+                ok = false;
+            if (!ok) return false;
+            tc::fence_after_sync();
+            if (lane == 0) {
+                const uint32_t a_row = a_lo0 + uint32_t(int(r % NS) * HP);  // (slot * HP * 16) >> 4
+                conv_row_mmas<CCH, NOUT, NS, HP>(j, sg.len, b0, [&](const ConvMma &m) {
+                    const uint32_t idesc = m.kb == m.ka ? IDESC1 : (m.kb == m.ka + 1 ? IDESC2 : IDESC3);
+                    tc::mma_bf16_lohi(tmem + uint32_t(m.blk * NOUT), a_row + m.a_off, a_hi, b_lo0 + m.b_off, b_hi,
+                                      idesc, uint32_t(m.acc));
+                });
+                tc::mma_commit(&empty_bar[r % NS]);  // the tensor cores are done with row r
+                const int bd = conv_row_done_block(j, on, NB);
+                if (bd >= 0) tc::mma_commit(&accf_bar[bd]);  // output row on - 2
             }
-            g += sg.len + 2;
-            o += sg.len;
-            u0 += sg.len;
-        }
+            __syncwarp();
+            return true;
+        });
         if (lane == 0) {
             tc::mma_commit(&done_bar);  // tracks every MMA issued above
             if (!tc::mbar_wait(&done_bar, 0u, CONV_WAIT_TRIES)) ok = false;
@@ -837,4 +888,57 @@ extern "C" qla_status qla_pack_conv_weights(const float *w, int nout, int cin, i
                                                    transpose_flip ? qla::PACK_ADJOINT : qla::PACK_PLAIN, packed,
                                                    static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? QLA_OK : QLA_ECUDA;
+}
+
+namespace qla {
+namespace {
+
+// Host-side walk of one CTA's MMA warp (the same helpers the kernel calls).
+template <int CCH, int NOUT>
+long long conv_schedule_t(int nimg, int H, int W, int grid, int cta, int *rec, long long cap) {
+    using L = ConvLayout<CCH, NOUT>;
+    constexpr int NB = L::NB, NS = L::NS, HP = L::HALO_PX;
+    const int TPR = W / 128;
+    const long long T = (long long)nimg * TPR * H;
+    const long long u_begin = T * cta / grid, u_end = T * (cta + 1) / grid;
+    long long n = 0;
+    auto put = [&](int type, long long r, long long on, int j, int len, int a, int b, int c, int d, int e, int f,
+                   uint32_t g, uint32_t h) {
+        if (n < cap) {
+            int *p = rec + n * QLA_CONV_SCHEDULE_FIELDS;
+            const int v[QLA_CONV_SCHEDULE_FIELDS] = {type, int(r), int(on), j, len, a, b, c, d, e, f, int(g), int(h), 0};
+            for (int k = 0; k < QLA_CONV_SCHEDULE_FIELDS; ++k) p[k] = v[k];
+        }
+        ++n;
+    };
+    conv_walk_rows(u_begin, u_end, H, TPR, [&](const ConvSeg &sg, int j, long long r, long long on) {
+        const int b0 = conv_block(on, NB);
+        uint32_t par = 0;
+        if (conv_row_acc_wait(j, sg.len, on, NB, &par)) put(2, r, on, j, sg.len, b0, int(par), 0, 0, 0, 0, 0, 0);
+        conv_row_mmas<CCH, NOUT, NS, HP>(j, sg.len, b0, [&](const ConvMma &m) {
+            put(0, r, on, j, sg.len, m.kx, m.k2, m.ka, m.kb, m.blk, m.acc, m.a_off, m.b_off);
+        });
+        put(3, r, on, j, sg.len, int(r % NS), 0, 0, 0, 0, 0, 0, 0);
+        const int bd = conv_row_done_block(j, on, NB);
+        if (bd >= 0) put(1, r, on, j, sg.len, bd, 0, 0, 0, 0, 0, 0, 0);
+        return true;
+    });
+    return n;
+}
+
+}  // namespace
+}  // namespace qla
+
+extern "C" qla_status qla_conv_schedule(int cin, int nout, int nimg, int H, int W, int grid, int cta, int *records,
+                                        long long capacity, long long *count) {
+    if (!count || nimg < 1 || H < 1 || W < 128 || W % 128 != 0 || grid < 1 || cta < 0 || cta >= grid ||
+        capacity < 0 || (capacity > 0 && !records) || (long long)nimg * H * (W / 128) > (1LL << 30))
+        return QLA_EINVAL;
+    long long n;
+    if (cin == 16 && nout == 64) n = qla::conv_schedule_t<2, 64>(nimg, H, W, grid, cta, records, capacity);
+    else if (cin == 64 && nout == 64) n = qla::conv_schedule_t<8, 64>(nimg, H, W, grid, cta, records, capacity);
+    else if (cin == 64 && nout == 16) n = qla::conv_schedule_t<8, 16>(nimg, H, W, grid, cta, records, capacity);
+    else return QLA_EUNSUPPORTED;
+    *count = n;
+    return QLA_OK;
 }

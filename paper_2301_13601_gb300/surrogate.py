@@ -14,7 +14,8 @@ EPI_GELU, EPI_LINEAR, EPI_DGRAD, EPI_QUPDATE = 0, 1, 2, 3
 DRIFT_PER_CALL, DRIFT_FROM_START = 0, 1
 ROLLOUT_SERIAL = 16  # flag: no speculative next call in qla_surrogate_rollout
 
-EXPORTS = ["qla_conv3x3_bf16", "qla_pack_conv_weights"]
+EXPORTS = ["qla_conv3x3_bf16", "qla_pack_conv_weights", "qla_conv_schedule"]
+CONV_SCHEDULE_FIELDS = 14  # ints per record of qla_conv_schedule
 
 _sigs_done = False
 
@@ -28,8 +29,29 @@ def lib():
         L.qla_conv3x3_bf16.restype = i
         L.qla_pack_conv_weights.argtypes = [v, i, i, i, i, i, v, v]
         L.qla_pack_conv_weights.restype = i
+        L.qla_conv_schedule.argtypes = [i, i, i, i, i, i, i, v, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+        L.qla_conv_schedule.restype = i
         _sigs_done = True
     return L
+
+
+def conv_schedule(cin: int, nout: int, nimg: int, H: int, W: int, grid: int, cta: int):
+    """The MMA issue schedule of one CTA of the conv kernel, enumerated on the
+    host by the code the kernel runs (see qla_conv_schedule): an int array
+    [records][CONV_SCHEDULE_FIELDS]. Touches no GPU."""
+    import numpy as np
+
+    L = lib()
+    count = ctypes.c_longlong()
+    st = L.qla_conv_schedule(cin, nout, nimg, H, W, grid, cta, None, 0, ctypes.byref(count))
+    if st != 0:
+        raise ValueError(f"qla_conv_schedule: status {st}")
+    rec = np.zeros((count.value, CONV_SCHEDULE_FIELDS), dtype=np.int32)
+    st = L.qla_conv_schedule(cin, nout, nimg, H, W, grid, cta, rec.ctypes.data_as(ctypes.c_void_p), count.value,
+                             ctypes.byref(count))
+    if st != 0 or count.value != rec.shape[0]:
+        raise ValueError(f"qla_conv_schedule: status {st}")
+    return rec
 
 
 def _ptr(t):
