@@ -30,12 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes per sweep launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of
-# the same kernel configuration on the 4096^2 version of the workload, scaled by 4 (the traffic of a
-# pass grows with the sites; profiles/sweep_kernel_cylinders8192_launches.md), valid while the
-# sweep's code (comment lines excluded), the workload, steps per pass and rows per tile match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "a4de286292ddbd32", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 2, "chunk_rows": 192, "bytes_per_launch": 4 * 1.9409e9}
+# DRAM bytes per sweep launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture
+# (one pass) of two sweep launches of this benchmark's own command on the 8192^2 workload
+# (profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
+# excluded), the workload, the steps per pass and the launch form (balanced split) match.
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "f8749235f454650b", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 8.21815e9}
 
 L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"
@@ -113,12 +113,16 @@ class ClockSampler:
 
 
 def sweep_code_hash() -> str:
-    """sha256 prefix of the sweep kernel source with its comment lines removed."""
+    """sha256 prefix of the sweep kernel's sources (the kernel, its
+    instantiations and launch split, the shared declarations) with their
+    comment lines removed."""
     import hashlib
 
-    with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", "qla_sweep.cuh")) as f:
-        code = "\n".join(l for l in f.read().splitlines() if not l.lstrip().startswith("//"))
-    return hashlib.sha256(code.encode()).hexdigest()[:16]
+    code = []
+    for name in ("qla_sweep.cuh", "qla_sweep_f32.cu", "qla_internal.h"):
+        with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", name)) as f:
+            code += [l for l in f.read().splitlines() if not l.lstrip().startswith("//")]
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def job_throughput(units: float, elapsed_ms: float, world: int, device=None):
@@ -271,7 +275,10 @@ def run_ours(args):
     # value): two contexts on their own streams, each stepping its own lattice
     # of the workload, so that one context's host copies overlap the other's
     # compute (qla_set_fields_f32 and qla_step are asynchronous on the
-    # context's stream; diagnostics and the read-back synchronise it).
+    # context's stream; diagnostics and the read-back synchronise it). The
+    # sweeps of the two contexts run one after the other (an event orders
+    # them): each pass of the balanced split is one wave of CTAs sized for
+    # the whole GPU, so two passes sharing the SMs would both run long.
     e2e_value = e2e_serial = None
     if not args.skip_extras:
         host = [torch.empty((6, w.Ny, w.Nx), dtype=torch.float32, pin_memory=True) for _ in range(2)]
@@ -293,14 +300,20 @@ def run_ours(args):
         sim2.step(S)
         sim2.diagnostics()
         torch.cuda.synchronize()
+        done = [torch.cuda.Event(), torch.cuda.Event()]
         t0 = time.perf_counter()
         sims[0].set_fields_host_f32(host[0].data_ptr())
         sims[0].step(S)
+        done[0].record(sims[0].stream)
         for i in range(2 * e2e_steps):  # 2 x e2e_steps bench steps, two in flight
             a, b = sims[i & 1], sims[(i + 1) & 1]
             if i + 1 < 2 * e2e_steps:
                 b.set_fields_host_f32(host[(i + 1) & 1].data_ptr())
+                # the copy overlaps a's sweeps; b's sweeps follow them (each
+                # pass is one wave of CTAs sized for the whole GPU)
+                b.stream.wait_event(done[i & 1])
                 b.step(S)
+                done[(i + 1) & 1].record(b.stream)
             a.diagnostics()
             a.get_fields_host_f32(host[i & 1].data_ptr())
         e2e_value = sites * S * 2 * e2e_steps * world / (time.perf_counter() - t0)

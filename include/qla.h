@@ -73,8 +73,9 @@ typedef struct {
     int potential;       /* QLA_POT_PAPER (default) or QLA_POT_UNITARY */
     int steps_per_pass;  /* full time steps fused per HBM pass: 0 = automatic (FP64: 2; FP32: 2 from
                             2^25 sites up, else 4), else 1, 2 or 4 */
-    int chunk_rows;      /* rows of one sweep tile: 0 = automatic (at most 256 rows at 2 steps a
-                            pass, 1024 otherwise), else >= 8 */
+    int chunk_rows;      /* rows of one sweep tile, else 0 = automatic: each family's rows are
+                            split into one share of equal estimated cost per resident CTA
+                            (see qla_sweep_split) */
     int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
     void *stream;        /* cudaStream_t to run on; NULL = a non-blocking stream owned by the context */
     int families;        /* QLA_FAMILIES_BOTH (default), or QLA_FAMILY_TM / QLA_FAMILY_TE: only that
@@ -249,9 +250,30 @@ qla_status qla_synchronize(qla_ctx *ctx);
 /* Steps taken since the last state reset; -1 for a NULL context. */
 long long qla_step_count(const qla_ctx *ctx);
 
-/* Resolved configuration: steps per pass and rows per tile used by qla_step,
- * and the precision. Any pointer may be NULL. */
+/* Resolved configuration: steps per pass and rows per tile used by qla_step
+ * (0: the balanced split), and the precision. Any pointer may be NULL. */
 qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_rows, int *precision);
+
+/* The balanced split of one fused pass of steps_per_pass steps (the sweep of
+ * Eq. 28 / Eq. 23 over the lattice, one CTA grid layer per family). The
+ * lattice is cut into strips of 256 - 8K output columns (K = steps_per_pass;
+ * a strip reads 256 columns, its halo included); row unit u = strip * Ny + y.
+ * Each of `ctas` CTAs per family sweeps the units [bounds[b], bounds[b + 1])
+ * of equal estimated cost (a row of a strip that wraps around x, copied
+ * without TMA, costs more; each strip start adds its warm-up rows).
+ * bounds: caller-owned, capacity >= ctas + 1 entries; bounds[0] = 0 and
+ * bounds[ctas] = strips * Ny. Host arithmetic only: needs no GPU.
+ * QLA_EINVAL on a bad size, precision, CTA count or capacity;
+ * QLA_EUNSUPPORTED if steps_per_pass is not instantiated for the precision. */
+qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, long long *bounds,
+                           int capacity);
+
+/* The split the context's passes of steps_per_pass steps use: *ctas = CTAs
+ * per family (0 when the context sweeps tiles of chunk_rows rows instead),
+ * and, if bounds is not NULL and *ctas > 0, the share bounds as
+ * qla_sweep_split writes them (capacity >= *ctas + 1). */
+qla_status qla_get_sweep_split(const qla_ctx *ctx, int steps_per_pass, int *ctas, long long *bounds,
+                               int capacity);
 
 /* Text of the last error on the context (empty string if none). */
 const char *qla_last_error(const qla_ctx *ctx);

@@ -56,9 +56,9 @@ def single_key(Nx: int, Ny: int, precision: str, sequence: str, potential: str, 
 
 
 def chunk_candidates(Ny: int, K: int) -> List[int]:
-    """Rows per tile to try: 0 (the library's wave-balancing choice) and a few
-    fixed heights between 16 K (warm-up at most a third) and the whole lattice
-    (finer around 256-512 rows, where two resident CTAs per SM measured best)."""
+    """Rows per tile to try: 0 (the balanced split: one equal-cost share of
+    each family's rows per resident CTA) and a few fixed tile heights between
+    16 K (warm-up at most a third) and the whole lattice."""
     out = {0}
     for h in (128, 192, 256, 320, 384, 512, 768, 1024, 2048, 4096):
         if 16 * K <= h < Ny:
@@ -113,7 +113,7 @@ def tune_single(n_x, n_y, n_z, delta: float, precision: str = "fp32", sequence: 
                 e1.record(sim.stream)
                 e1.synchronize()
                 sec = e0.elapsed_time(e1) / 1e3 / (repeats * s)
-            results.append(({"steps_per_pass": K, "chunk_rows": ch or sim.chunk_rows}, sec))
+            results.append(({"steps_per_pass": K, "chunk_rows": ch}, sec))
     cfg, sec = pick_best(results)
     entry = dict(cfg, seconds_per_step=sec, site_updates_per_s=Nx * Ny / sec, tuned_at=time.time())
     if use_cache:

@@ -32,6 +32,7 @@ struct qla_ctx {
     size_t esize = 4;
     int K = 4;
     int chunk = 0;
+    int ctas[5] = {0, 0, 0, 0, 0};  // balanced split (chunk == 0): CTAs per family of a pass of K steps
     long long steps = 0;
     bool has_state = false;
     qla_status sticky = QLA_OK;
@@ -109,39 +110,12 @@ int default_steps_per_pass(int precision, int Nx, int Ny) {
     return (long long)Nx * Ny >= (1LL << 25) ? 2 : 4;
 }
 
-// Rows per tile: the fewest waves x (rows + warm-up rows) among tiles of at
-// most max_auto_chunk(K) rows. The caps are measured, not modelled: on the
-// 8192^2 workload tiles of 512-1280 rows (K = 4) beat the few-wave splits the
-// wave model alone prefers (39-40 G vs 36 G for 4096 rows), and with K = 2
-// (two CTAs per SM) tiles of 192-200 rows run 74.7 G against 74.3 G for 176,
-// 73.9 G for 216, 73.7 G for 232 and 72.8 G for 256 (the model then picks 192).
-int max_auto_chunk(int K) { return K == 2 ? 200 : 1024; }
-
-int auto_chunk(int Nx, int Ny, int K, int prec, int sms) {
-    const int kMaxAutoChunk = max_auto_chunk(K);
-    const int W = qla::sweep_strip_width();
-    const int wv = W - 8 * K;
-    const int nsx = (Nx + wv - 1) / wv;
-    const int occ = prec ? qla::sweep_occupancy_f64(K, 1) : qla::sweep_occupancy_f32(K, 1);
-    const long long slots = (long long)sms * occ;
-    double best = 1e300;
-    int best_chunk = std::min(Ny, kMaxAutoChunk);
-    for (int ncy = 1; ncy <= std::max(1, Ny / 8); ++ncy) {
-        int ch = (Ny + ncy - 1) / ncy;
-        ch = (ch + 7) / 8 * 8;
-        if (ch > Ny) ch = Ny;
-        if (ch > kMaxAutoChunk) continue;
-        const int real_ncy = (Ny + ch - 1) / ch;
-        const long long ctas = (long long)nsx * real_ncy * 2;
-        const long long waves = (ctas + slots - 1) / slots;
-        const double cost = double(waves) * double(ch + 8 * K + 8 * (K - 1));
-        if (cost < best * 0.999) {
-            best = cost;
-            best_chunk = ch;
-        }
-        if (ctas > 64 * slots && best < 1e300) break;
-    }
-    return std::max(1, best_chunk);
+// CTAs per family of the balanced split of a pass of K steps: one per
+// resident slot (SMs x CTAs per SM), at most one per row unit.
+int balanced_ctas(int Nx, int Ny, int K, int prec, int interleaved, int sms) {
+    const int occ = prec ? qla::sweep_occupancy_f64(K, interleaved) : qla::sweep_occupancy_f32(K, interleaved);
+    const qla::SweepSplit sp = qla::make_sweep_split(Nx, Ny, K, qla::sweep_block_rows(prec, K), prec ? 0 : 1);
+    return int(std::min((long long)sms * occ, (long long)sp.nsx * Ny));
 }
 
 // Whether component `comp` (Eq. 15 order) belongs to a family the context
@@ -161,6 +135,7 @@ qla_status launch_pass(qla_ctx *c, int K) {
     a.Ny = c->Ny;
     a.w_valid = qla::sweep_strip_width() - 8 * K;
     a.chunk = c->chunk;
+    a.ctas = c->ctas[K];
     a.interleaved = c->opt.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0;
     a.unitary = c->opt.potential == QLA_POT_UNITARY ? 1 : 0;
     a.vec = (c->Nx % int(16 / c->esize)) == 0 ? 1 : 0;
@@ -316,8 +291,12 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
         return bail(QLA_ECUDA);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(QLA_ECUDA);
     c->K = o.steps_per_pass > 0 ? o.steps_per_pass : default_steps_per_pass(o.precision, Nx, Ny);
-    c->chunk = o.chunk_rows > 0 ? std::min(o.chunk_rows, Ny)
-                                : auto_chunk(Nx, Ny, c->K, o.precision == QLA_FP64 ? 1 : 0, sm_count(c->dev));
+    c->chunk = o.chunk_rows > 0 ? std::min(o.chunk_rows, Ny) : 0;
+    if (c->chunk == 0)
+        for (int k = 1; k <= 4; ++k)
+            if (qla::sweep_supported(o.precision, k))
+                c->ctas[k] = balanced_ctas(Nx, Ny, k, o.precision == QLA_FP64 ? 1 : 0,
+                                           o.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0, sm_count(c->dev));
     c->has_state = true;  // zero state
     *out = c;
     return QLA_OK;
@@ -528,6 +507,33 @@ qla_status qla_get_config(const qla_ctx *c, int *steps_per_pass, int *chunk_rows
     if (chunk_rows) *chunk_rows = c->chunk;
     if (precision) *precision = c->opt.precision;
     return QLA_OK;
+}
+
+namespace {
+qla_status write_split(const qla::SweepSplit &sp, int ctas, long long *bounds, int capacity) {
+    if (ctas < 1 || !bounds || capacity < ctas + 1) return QLA_EINVAL;
+    for (int b = 0; b <= ctas; ++b) bounds[b] = sp.share_begin(b, ctas);
+    return QLA_OK;
+}
+}  // namespace
+
+qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, long long *bounds,
+                           int capacity) {
+    if (Nx < 1 || Ny < 1 || (precision != QLA_FP32 && precision != QLA_FP64)) return QLA_EINVAL;
+    if (!qla::sweep_supported(precision, steps_per_pass)) return QLA_EUNSUPPORTED;
+    const int prec = precision == QLA_FP64 ? 1 : 0;
+    const qla::SweepSplit sp =
+        qla::make_sweep_split(Nx, Ny, steps_per_pass, qla::sweep_block_rows(prec, steps_per_pass), prec ? 0 : 1);
+    if ((long long)sp.nsx * Ny >= (1LL << 31)) return QLA_EINVAL;
+    return write_split(sp, ctas, bounds, capacity);
+}
+
+qla_status qla_get_sweep_split(const qla_ctx *c, int steps_per_pass, int *ctas, long long *bounds, int capacity) {
+    if (!c || !ctas) return QLA_EINVAL;
+    if (!qla::sweep_supported(c->opt.precision, steps_per_pass)) return QLA_EUNSUPPORTED;
+    *ctas = c->chunk > 0 ? 0 : c->ctas[steps_per_pass];
+    if (*ctas == 0 || !bounds) return QLA_OK;
+    return qla_sweep_split(c->Nx, c->Ny, c->opt.precision, steps_per_pass, *ctas, bounds, capacity);
 }
 
 const char *qla_last_error(const qla_ctx *c) { return c ? c->msg.c_str() : "NULL context"; }

@@ -147,12 +147,13 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
         // the input rows were written by other CTAs (generic proxy) and are
         // read here by TMA loads (async proxy)
         asm volatile("fence.proxy.async;\n" ::: "memory");
-        if (fam == 0)
-            sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, chunk, smem_raw, M ? &M->m[par] : nullptr,
-                                                    I.merged != 0);
-        else
-            sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, chunk, smem_raw, M ? &M->m[par] : nullptr,
-                                                    I.merged != 0);
+        const int yb = chunk * I.chunk, ye = min(yb + I.chunk, I.Ny);
+        const bool failed =
+            fam == 0 ? sweep_body<T, K, R, NY, INTER, UNIT, 0>(a, strip, yb, ye, smem_raw, M ? &M->m[par] : nullptr,
+                                                               I.merged != 0)
+                     : sweep_body<T, K, R, NY, INTER, UNIT, 1>(a, strip, yb, ye, smem_raw, M ? &M->m[par] : nullptr,
+                                                               I.merged != 0);
+        if (failed) break;  // the error flag is set: every CTA stops at its next work item
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -80,6 +80,7 @@ struct SweepParams {
     int tma;
     int merged;
     int tiles_fastest;  // grid x runs over the row tiles of a strip (else over the strips of a tile row)
+    SweepSplit split;  // balanced split (a.chunk == 0)
 };
 
 template <typename T>
@@ -408,8 +409,12 @@ struct YPipe {
     }
 };
 
+// One tile: output rows [yb, ye) of a strip, level 0 fed from yb - 4K.
+// Returns true (uniformly over the CTA) if the error flag is set (a bounded
+// copy wait ran out); the CTA's copy barriers are then left as they are and
+// the caller stops.
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
-__device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int chunk_idx, unsigned char *smem_raw,
+__device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb, int ye, unsigned char *smem_raw,
                                            const SweepMaps *M = nullptr, bool merged = false) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
@@ -444,8 +449,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
     const int xbase = xs0 - 4 * K;            // global column of strip column 0 (may be < 0)
     const int xb = wrapi(xbase, Nx);
     const bool nowrap = xbase >= 0 && xbase + W_IN <= Nx;
-    const int yb = chunk_idx * A.chunk;
-    const int ye = min(yb + A.chunk, Ny);
     const int F0 = yb - 4 * K;                // first row fed to level 0
     const int nit = (ye - yb + 8 * K + R - 1) / R + K - 1;
 
@@ -859,6 +862,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &A, int strip, int ch
         }
         __syncthreads();
     }
+    // every copy issued was waited for: the barriers are idle unless a wait
+    // ran out (here or in another CTA; the pass's results are then invalid)
+    const bool failed = A.error && __syncthreads_or(*reinterpret_cast<volatile int *>(A.error) != 0);
+    if (use_tma && !failed && tid == 0) {
+        tc::mbar_inval(&tbar[0]);
+        tc::mbar_inval(&tbar[1]);
+    }
+    return failed;
 }
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
@@ -866,12 +877,28 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
     sweep_kernel(const __grid_constant__ SweepParams prm) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const SweepMaps *maps = prm.tma ? &prm.m : nullptr;
-    const int strip = prm.tiles_fastest ? blockIdx.y : blockIdx.x;
-    const int chunk = prm.tiles_fastest ? blockIdx.x : blockIdx.y;
-    if (prm.a.fam0 + int(blockIdx.z) == 0)
-        sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, strip, chunk, smem_raw, maps, prm.merged != 0);
-    else
-        sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, strip, chunk, smem_raw, maps, prm.merged != 0);
+    const int Ny = prm.a.Ny;
+    int u, u1;  // this CTA's row units [u, u1) (nsx * Ny < 2^31, checked on the host)
+    if (prm.a.chunk <= 0) {
+        u = int(prm.split.share_begin(blockIdx.x, gridDim.x));
+        u1 = int(prm.split.share_begin(blockIdx.x + 1, gridDim.x));
+    } else {
+        const int strip = prm.tiles_fastest ? blockIdx.y : blockIdx.x;
+        const int chunk = prm.tiles_fastest ? blockIdx.x : blockIdx.y;
+        u = strip * Ny + chunk * prm.a.chunk;
+        u1 = min(u + prm.a.chunk, (strip + 1) * Ny);
+    }
+    while (u < u1) {
+        const int s = u / Ny;
+        const int y0 = u - s * Ny;
+        const int y1 = min(Ny, y0 + (u1 - u));
+        const bool failed =
+            prm.a.fam0 + int(blockIdx.z) != 0
+                ? sweep_body<T, K, R, NY, INTER, UNIT, 1>(prm.a, s, y0, y1, smem_raw, maps, prm.merged != 0)
+                : sweep_body<T, K, R, NY, INTER, UNIT, 0>(prm.a, s, y0, y1, smem_raw, maps, prm.merged != 0);
+        if (failed) break;
+        u += y1 - y0;
+    }
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -972,6 +999,15 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value)
         prm.tma = (a.error != nullptr && make_sweep_maps(a, K, R, prm.m, &prm.merged)) ? 1 : 0;
     const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
+    if (a.chunk <= 0) {
+        // balanced: a.ctas CTAs per family (one per resident slot), each one
+        // equal share of its family's rows: no tail wave, and the warm-up
+        // rows once per share and strip instead of once per tile
+        prm.split = make_sweep_split(a.Nx, a.Ny, K, R, std::is_same<T, float>::value ? 1 : 0);
+        if (a.ctas < 1 || (long long)prm.split.nsx * a.Ny >= (1LL << 31)) return cudaErrorInvalidValue;
+        sweep_kernel<T, K, R, NY, INTER, UNIT><<<dim3(unsigned(a.ctas), 1, nfam), Cfg::NT, L::SMEM, st>>>(prm);
+        return cudaGetLastError();
+    }
     const int ncy = (a.Ny + a.chunk - 1) / a.chunk;
     // CTA order. One 224 KB CTA per SM (K = 4): the tiles of a strip in a row,
     // so that a tile's warm-up rows were just read by its neighbour above

@@ -36,7 +36,8 @@ EXPORTS = [
     "qla_set_fields_f32", "qla_step", "qla_debug_apply", "qla_energy", "qla_divB", "qla_divD", "qla_diagnostics",
     "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
-    "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc",
+    "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc", "qla_sweep_split",
+    "qla_get_sweep_split",
     "qla_batch_create", "qla_batch_run", "qla_batch_get_fields_f32", "qla_batch_diagnostics", "qla_batch_info",
     "qla_batch_set_wait_limit", "qla_batch_last_error", "qla_batch_destroy",
 ]
@@ -126,8 +127,25 @@ def load_library(path: str = LIB_PATH):
     L.qla_destroy.restype = None
     L.qla_diagnostics_noalloc.argtypes = [v, i, i, i, v, P(Diag)]
     L.qla_diagnostics_noalloc.restype = st
+    L.qla_sweep_split.argtypes = [i, i, i, i, i, P(ctypes.c_longlong), i]
+    L.qla_sweep_split.restype = st
+    L.qla_get_sweep_split.argtypes = [v, i, P(i), P(ctypes.c_longlong), i]
+    L.qla_get_sweep_split.restype = st
     _lib = L
     return L
+
+
+def sweep_split(Nx: int, Ny: int, steps_per_pass: int, ctas: int, precision: str = "fp32") -> np.ndarray:
+    """Share bounds of the balanced split of an Nx x Ny pass of steps_per_pass
+    steps over `ctas` CTAs per family (host arithmetic of the library; no GPU)."""
+    L = load_library()
+    out = np.zeros(int(ctas) + 1, dtype=np.int64)
+    st = L.qla_sweep_split(int(Nx), int(Ny), _code("precision", {"fp32": FP32, "fp64": FP64}, precision),
+                           int(steps_per_pass), int(ctas), out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                           out.size)
+    if st != 0:
+        raise QLAError(st, "qla_sweep_split")
+    return out
 
 
 def _dptr(a: np.ndarray):
@@ -302,6 +320,22 @@ class Simulation:
 
     def synchronize(self):
         self._check(self._L.qla_synchronize(self._ctx), "qla_synchronize")
+
+    def sweep_split(self, steps_per_pass: Optional[int] = None) -> Optional[np.ndarray]:
+        """Share bounds (row units u = strip * Ny + y, one share per CTA of a
+        family) of the balanced split that passes of steps_per_pass steps use
+        (default: the configured steps per pass); None when the context sweeps
+        fixed tiles of chunk_rows rows."""
+        K = int(steps_per_pass or self.steps_per_pass)
+        n = ctypes.c_int()
+        self._check(self._L.qla_get_sweep_split(self._ctx, K, ctypes.byref(n), None, 0), "qla_get_sweep_split")
+        if n.value == 0:
+            return None
+        out = np.zeros(n.value + 1, dtype=np.int64)
+        self._check(self._L.qla_get_sweep_split(self._ctx, K, ctypes.byref(n),
+                                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), out.size),
+                    "qla_get_sweep_split")
+        return out
 
     @property
     def step_count(self) -> int:

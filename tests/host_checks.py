@@ -80,3 +80,14 @@ def noalloc_rejects_sizes_beyond_its_scratch():
     assert L.qla_diagnostics_noalloc(dummy, FP64, 70000, 70000, None, ctypes.byref(d)) == 1
     assert L.qla_diagnostics_noalloc(dummy, 7, 8, 8, None, ctypes.byref(d)) == 1
     assert L.qla_diagnostics_noalloc(None, FP32, 8, 8, None, ctypes.byref(d)) == 1
+
+
+def sweep_split_is_host_arithmetic():
+    import numpy as np
+
+    from paper_2301_13601_gb300 import qla
+
+    b = qla.sweep_split(8192, 8192, 2, 304)
+    assert b[0] == 0 and b[-1] == 35 * 8192 and np.all(np.diff(b) > 0)
+    b64 = qla.sweep_split(8192, 8192, 2, 304, "fp64")
+    assert b64[-1] == b[-1]

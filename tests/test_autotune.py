@@ -32,7 +32,7 @@ def test_tune_single_returns_a_working_config(tmp_path, monkeypatch):
     monkeypatch.setenv(autotune.CACHE_ENV, str(tmp_path / "c.json"))
     n = media.smooth_periodic_medium(512, 384, seed=1)
     best = autotune.tune_single(*n, 0.05, ks=(2, 4), steps=8, repeats=2)
-    assert best["steps_per_pass"] in (2, 4) and best["chunk_rows"] > 0
+    assert best["steps_per_pass"] in (2, 4) and best["chunk_rows"] in autotune.chunk_candidates(384, best["steps_per_pass"])
     assert best["site_updates_per_s"] > 0
     again = autotune.tune_single(*n, 0.05, ks=(2, 4), steps=8, repeats=2)
     assert again == best  # served from the cache

@@ -38,9 +38,11 @@ def oracle_run(n, q0, delta, steps, sequence="interleaved", potential="paper"):
     return q
 
 
-# lattice shapes: several strips with a ragged tail and several row chunks,
-# odd sizes (scalar-load path), a tiny lattice narrower than a strip
-SHAPES = [(500, 70, 24), (37, 53, 0), (8, 5, 0), (64, 64, 16)]
+# lattice shapes (Nx, Ny, rows per tile; 0 = the balanced split): several
+# strips with a ragged tail and several row chunks, the same under the
+# balanced split (shares spanning strips), odd sizes (scalar-load path), a
+# tiny lattice narrower than a strip (fewer row units than CTA slots)
+SHAPES = [(500, 70, 24), (500, 70, 0), (37, 53, 0), (8, 5, 0), (64, 64, 16)]
 
 
 def problem(Nx, Ny, seed=3):
@@ -82,11 +84,13 @@ def test_fp32_matches_oracle(shape, K, sequence, potential):
 @pytest.mark.parametrize("K", [2, 4])
 @pytest.mark.parametrize("sequence", ["interleaved", "plain"])
 @pytest.mark.parametrize("potential", ["paper", "unitary"])
-def test_fp32_tma_strips_match_oracle(K, sequence, potential):
+@pytest.mark.parametrize("chunk", [40, 0])
+def test_fp32_tma_strips_match_oracle(K, sequence, potential, chunk):
     """Nx a multiple of 8 and several strips: the inner strips load their rows
     with TMA, the two that wrap around x with cp.async; both must agree with
-    the oracle (rows in tiles of 40 with a ragged last tile)."""
-    Nx, Ny, chunk = 1024, 96, 40
+    the oracle (rows in tiles of 40 with a ragged last tile, or the balanced
+    split: shares that start and end inside strips and span strip ends)."""
+    Nx, Ny = 1024, 96
     n, q0 = problem(Nx, Ny, seed=5)
     delta, steps = 0.2, 3 * K + 1
     got = gpu_run(n, q0, delta, steps, precision="fp32", steps_per_pass=K, chunk_rows=chunk,
@@ -110,6 +114,32 @@ def test_fp32_tma_block_boxes_match_oracle(K, Ny, chunk):
     got = gpu_run(n, q0, delta, steps, precision="fp32", steps_per_pass=K, chunk_rows=chunk)
     ref = oracle_run(n, q0, delta, steps, "interleaved", "paper")
     assert rel_l2(got, ref) < 3e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("Nx, Ny", [(1000, 777), (2048, 300)])
+def test_balanced_split_equals_tiles_bit_exact(precision, Nx, Ny):
+    """Every output site is computed by the same operations in the same order
+    whichever CTA sweeps it (a tile or a share of the balanced split, warm-up
+    rows included), so the two launch forms agree bit for bit."""
+    n, q0 = problem(Nx, Ny, seed=11)
+    K = 2
+    a = gpu_run(n, q0, 0.2, 4 * K, precision=precision, steps_per_pass=K, chunk_rows=0)
+    b = gpu_run(n, q0, 0.2, 4 * K, precision=precision, steps_per_pass=K, chunk_rows=56)
+    assert np.array_equal(a, b)
+
+
+def test_balanced_split_covers_the_units():
+    """The context's split: one share per resident slot, bounds tiling the
+    strips x rows, and a context with chunk_rows set reports no split."""
+    n, q0 = problem(2048, 300, seed=2)
+    with Simulation(*n, 0.2, precision="fp32", steps_per_pass=2) as sim:
+        b = sim.sweep_split()
+        nsx = -(-2048 // 240)
+        assert b is not None and b[0] == 0 and b[-1] == nsx * 300 and np.all(np.diff(b) >= 0)
+        assert b.size - 1 <= nsx * 300
+    with Simulation(*n, 0.2, precision="fp32", steps_per_pass=2, chunk_rows=64) as sim:
+        assert sim.sweep_split() is None and sim.chunk_rows == 64
 
 
 def test_pulse_init_matches_oracle():
@@ -283,24 +313,36 @@ def window(a, yc, xc, H):
     return np.ascontiguousarray(a[..., ys[:, None], xs[None, :]])
 
 
+def share_seams(sim, Ny, shares, W=240):
+    """(row, column) sites on the seam between share b - 1 and share b of the
+    balanced split, for each b in shares: the first row of share b, in the
+    middle of its strip's columns."""
+    bounds = sim.sweep_split()
+    out = []
+    for b in shares:
+        s, y = divmod(int(bounds[b]), Ny)
+        out.append((y, s * W + W // 2))
+    return out
+
+
 def test_cylinders_8192_sampled_parity():
     w = media.workload_cylinders_8192()
     n = w.medium()
     steps = 8  # four fused passes of 2 steps, the automatic configuration at this size
     with Simulation(*n, w.delta, precision="fp32") as sim:
-        assert sim.steps_per_pass == 2 and sim.chunk_rows <= 256
-        ch = sim.chunk_rows
+        assert sim.steps_per_pass == 2 and sim.chunk_rows == 0
+        seams = share_seams(sim, 8192, [1, 2, 40, 157, 303])
         sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
         q0 = sim.get_fields()
         sim.step(steps)
         got = sim.get_fields(dtype=np.float32)
     H = 4 * steps + 8
     # sample sites: pulse flank, object edges, lattice corners (periodic wrap),
-    # strip seams (240 written columns per strip) and tile seams (ch rows)
+    # strip seams (240 written columns per strip) and the seams between the
+    # CTA shares of the balanced split (rows where one CTA's share ends)
     obj = w.objects[0]
     samples = [(4096, 1024 + 100), (0, 0), (8191, 8191), (int(obj.cy), int(obj.cx - obj.a)),
-               (int(obj.cy + obj.b), int(obj.cx)), (1234, 240), (4096, 239), (8000, 8180),
-               (3 * ch, 4080), (20 * ch - 1, 1000)]
+               (int(obj.cy + obj.b), int(obj.cx)), (1234, 240), (4096, 239), (8000, 8180)] + seams
     for yc, xc in samples:
         nw = tuple(window(a, yc, xc, H) for a in n)
         qw = window(q0, yc, xc, H)
@@ -315,7 +357,7 @@ def test_cylinders_8192_sampled_parity():
 def test_cylinders_8192_sampled_parity_200_steps():
     """The first 200 steps of the 8192^2 workload in the benchmark's launch
     configuration, on five sampled windows where the pulse is (the dependency
-    window after 200 steps is 1601^2 sites): the pulse flank, a tile seam, a
+    window after 200 steps is 1601^2 sites): the pulse flank, a share seam, a
     strip seam, the periodic y-wrap and the pulse's far flank. FP32 bound:
     about 64 roundings of 2^-24 per component and step, a random walk of
     6e-8 * sqrt(64 * 200) = 7e-6 of the local amplitude; 1e-5 is asserted."""
@@ -324,14 +366,17 @@ def test_cylinders_8192_sampled_parity_200_steps():
     steps = 200
     with Simulation(*n, w.delta, precision="fp32") as sim:
         assert sim.steps_per_pass == 2
-        ch = sim.chunk_rows
+        bounds = sim.sweep_split()
         sim.init_pulse("Ez", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
         q0 = sim.get_fields()
         sim.step(steps)
         got = sim.get_fields(dtype=np.float32)
     H = 4 * steps + 8
     x0 = int(w.pulse.x0)
-    samples = [(4096, x0 + 60), (5 * ch, x0 - 40), (3000, 960), (0, x0 + 10), (8191, x0 - 120)]
+    # a share seam inside the pulse's strip: the first share that starts in it below row 4096
+    strip = (x0 - 40) // 240
+    seam = next(int(u) % 8192 for u in bounds if int(u) // 8192 == strip and int(u) % 8192 > 4096)
+    samples = [(4096, x0 + 60), (seam, x0 - 40), (3000, 960), (0, x0 + 10), (8191, x0 - 120)]
     for yc, xc in samples:
         nw = tuple(window(a, yc, xc, H) for a in n)
         qw = window(q0, yc, xc, H)
