@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 # (one pass) of two sweep launches of this benchmark's own command on the 8192^2 workload
 # (profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
 # excluded), the workload, the steps per pass and the launch form (balanced split) match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "f8749235f454650b", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 8.21815e9}
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "0f839fbf79fbd9bf", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 7.79978e9}
 
 L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"

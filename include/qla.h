@@ -72,7 +72,7 @@ typedef struct {
     int sequence;        /* QLA_SEQ_INTERLEAVED (default, Eq. 28) or QLA_SEQ_PLAIN (Eq. 23) */
     int potential;       /* QLA_POT_PAPER (default) or QLA_POT_UNITARY */
     int steps_per_pass;  /* full time steps fused per HBM pass: 0 = automatic (FP64: 2; FP32: 2 from
-                            2^25 sites up, else 4), else 1, 2 or 4 */
+                            2^20 sites up (2^25 with chunk_rows set), else 4), else 1, 2 or 4 */
     int chunk_rows;      /* rows of one sweep tile, else 0 = automatic: each family's rows are
                             split into one share of equal estimated cost per resident CTA
                             (see qla_sweep_split) */
@@ -257,10 +257,12 @@ qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_ro
 /* The balanced split of one fused pass of steps_per_pass steps (the sweep of
  * Eq. 28 / Eq. 23 over the lattice, one CTA grid layer per family). The
  * lattice is cut into strips of 256 - 8K output columns (K = steps_per_pass;
- * a strip reads 256 columns, its halo included); row unit u = strip * Ny + y.
- * Each of `ctas` CTAs per family sweeps the units [bounds[b], bounds[b + 1])
- * of equal estimated cost (a row of a strip that wraps around x, copied
- * without TMA, costs more; each strip start adds its warm-up rows).
+ * a strip reads 256 columns, its halo included); in FP32 with K >= 2 and Nx a
+ * multiple of 8, at least 256, strip 0 straddles the periodic seam x = 0 and
+ * strips 1.. cover the columns between. Row unit u = strip * Ny + y. Each of
+ * `ctas` CTAs per family sweeps the units [bounds[b], bounds[b + 1]) of equal
+ * cost (one per row, plus the 8K + R (K - 1) warm-up rows, R = 4 (8 for FP32
+ * at K = 1), at each strip start).
  * bounds: caller-owned, capacity >= ctas + 1 entries; bounds[0] = 0 and
  * bounds[ctas] = strips * Ny. Host arithmetic only: needs no GPU.
  * QLA_EINVAL on a bad size, precision, CTA count or capacity;

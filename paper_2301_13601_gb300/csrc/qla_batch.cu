@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
         a.Ny = I.Ny;
         a.w_valid = I.w_valid;
         a.chunk = I.chunk;
+        a.ctas = 0;
+        a.seam = 0;  // strips in the plain layout (the two at the x-edges copy with cp.async)
         a.interleaved = INTER ? 1 : 0;
         a.unitary = UNIT ? 1 : 0;
         a.vec = I.vec;

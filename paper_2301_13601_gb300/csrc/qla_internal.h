@@ -45,56 +45,39 @@ struct Family {
     int vx_hub, vy_hub;       // 1 if the potential row targets the hub, 0 if the partner
 };
 
-// Balanced split of a pass. The row units u = strip * Ny + y of a family
-// (nsx strips of w_valid output columns, Ny rows each) are shared among the
-// CTAs of the family's grid layer in equal shares of estimated cost; a CTA
-// sweeps its units as one segment per strip it touches. Cost, in sixteenths
-// of a row: 16 per row of a strip that copies with TMA, w_slow per row of a
-// strip that copies with cp.async (FP32 strips that wrap around x; with no
-// TMA at all every row costs 16), and 16 * warm at each strip's start (the
-// warm-up rows a segment that starts there sweeps in addition).
+// Strips and balanced split of a pass. The row units u = strip * Ny + y of
+// a family (nsx strips, Ny rows each) are shared among the CTAs of the
+// family's grid layer in equal shares of cost; a CTA sweeps its units as one
+// segment per strip it touches. Cost, in rows: one per row, plus `warm` at
+// each strip's start (the warm-up rows a segment that starts there sweeps in
+// addition). Every strip of a pass costs the same per row: with the seam
+// layout all of them copy with TMA, and without it (FP64; FP32 with K = 1, Nx
+// not a multiple of 8, or Nx < W_IN) none does.
 struct SweepSplit {
     int Nx, Ny;
-    int w_valid;          // output columns per strip
-    int w_in;             // input columns per strip (w_valid + 8K)
-    int nsx;              // strips
-    int warm;             // warm-up rows of a segment: 8K + R (K - 1)
-    int w_slow;
-    int tma;              // FP32 with Nx a multiple of 8: strips inside [0, Nx) copy with TMA
-    long long cost_total; // the sum of strip_cost over the strips
+    int w_valid;  // output columns per strip
+    int nsx;      // strips
+    int warm;     // warm-up rows of a segment: 8K + R (K - 1)
+    int seam;     // the seam layout (SweepArgs::seam)
 
-    // whether strip s copies with TMA (the kernel's test: its input columns
-    // lie inside [0, Nx) and start 8-aligned)
-    __host__ __device__ bool strip_uses_tma(int s) const {
-        const int xbase = s * w_valid - (w_in - w_valid) / 2;
-        return tma && xbase >= 0 && xbase + w_in <= Nx && (xbase & 7) == 0;
-    }
-    __host__ __device__ long long strip_row_cost(int s) const { return !tma || strip_uses_tma(s) ? 16 : w_slow; }
-    __host__ __device__ long long strip_cost(int s) const { return 16LL * warm + strip_row_cost(s) * Ny; }
-    // The smallest unit whose cost prefix reaches c (0 <= c <= cost_total):
-    // the shares [unit(C b / G), unit(C (b + 1) / G)), b = 0 .. G - 1, tile
-    // the nsx * Ny units exactly.
+    __host__ __device__ long long cost_total() const { return (long long)nsx * (Ny + warm); }
+    // The row unit at cost position c (0 <= c <= cost_total(); a position
+    // inside a strip's warm-up maps to the strip's first row): monotonic, so
+    // the shares [unit(C b / G), unit(C (b + 1) / G)), b = 0 .. G - 1, tile the
+    // nsx * Ny units exactly.
     __host__ __device__ long long unit_of_cost(long long c) const {
-        long long base = 0;
-        for (int s = 0; s < nsx; ++s) {
-            const long long cs = strip_cost(s);
-            if (c <= base + cs) {
-                const long long r = c - base - 16LL * warm;  // cost into the strip's rows
-                if (r <= 0) return (long long)s * Ny;
-                const long long w = strip_row_cost(s);
-                const long long y = (r + w - 1) / w;
-                return (long long)s * Ny + (y < Ny ? y : Ny);
-            }
-            base += cs;
-        }
-        return (long long)nsx * Ny;
+        const long long per = Ny + warm;
+        const long long s = c / per;
+        if (s >= nsx) return (long long)nsx * Ny;
+        const long long r = c - s * per - warm;  // rows of strip s covered
+        return s * Ny + (r <= 0 ? 0 : r);
     }
-    __host__ __device__ long long share_begin(int b, int G) const { return unit_of_cost(cost_total * b / G); }
+    __host__ __device__ long long share_begin(int b, int G) const { return unit_of_cost(cost_total() * b / G); }
 };
 
-// The split of a pass of K steps (R rows per iteration) over an Nx x Ny
-// lattice; w_slow from the measured cost of the cp.async strips.
-SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int fp32);
+// The strips and split of a pass of K steps (R rows per iteration) over an
+// Nx x Ny lattice; tma: the pass may copy with TMA (FP32 with its tensor maps).
+SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma);
 // Rows per iteration R of the sweep instantiated for (precision, K).
 int sweep_block_rows(int precision, int K);
 
@@ -106,6 +89,14 @@ struct SweepArgs {
     int w_valid;        // output columns per strip
     int chunk;          // output rows per tile (tiled grid); 0: balanced split over `ctas` CTAs per family
     int ctas;           // balanced split: CTAs per family
+    // Strip layout. 0: strip s reads input columns [s w_valid - 4K, + W_IN)
+    // (the first and the last strip wrap around x). 1 (the seam layout, FP32
+    // with TMA, Nx >= W_IN, a multiple of 8): strip 0 straddles the periodic
+    // seam, reading columns [Nx - W_IN/2, Nx) and [0, W_IN/2) and writing the
+    // w_valid in their middle; strips s >= 1 cover the outputs between,
+    // strip s from column W_IN/2 - 4K + (s - 1) w_valid, the last one's input
+    // moved left to end at Nx at the latest (it writes only its own columns).
+    int seam;
     int interleaved;    // 1: Eq. 28, 0: Eq. 23
     int unitary;        // 1: unitary potentials
     int vec;            // 1: 16-byte vector access is legal (Nx multiple of 16/sizeof(T))

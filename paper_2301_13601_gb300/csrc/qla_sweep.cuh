@@ -72,6 +72,18 @@ struct SweepMaps {
     // valid when merged != 0 (K > 1 and Ny a multiple of R + 4).
     CUtensorMap coef_m1;
     CUtensorMap coef_m2;
+    // The seam strip (SweepArgs::seam) reads columns [Nx - 128, Nx) and
+    // [0, 128). These views see a row as two 128-column halves, half 0 at
+    // column 0 and half 1 at column Nx - 128 ({e, 16, 2, Ny, planes}, the half
+    // stride (Nx - 128) elements), so one box brings both halves. They land
+    // swapped (global columns 0..127 first): the kernel addresses the seam
+    // strip's shared rows at column c ^ 128.
+    CUtensorMap seam_state;     // one row of one component
+    CUtensorMap seam_state_r1;  // R rows of 1, 2, 3 adjacent components
+    CUtensorMap seam_state_r2;
+    CUtensorMap seam_state_r3;
+    CUtensorMap seam_coef;      // one row of one pair plane
+    CUtensorMap seam_coef_r;    // R rows of one pair plane
 };
 
 struct SweepParams {
@@ -445,10 +457,29 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
     const int lane = tid & 31;
     const int warp = tid >> 5;
 
-    const int xs0 = strip * A.w_valid;   // first output column of the strip
-    const int xbase = xs0 - 4 * K;            // global column of strip column 0 (may be < 0)
+    // strip geometry (SweepArgs::seam): xbase = global column of strip column
+    // 0 (may be < 0), [o_lo, o_hi) = the global columns the strip writes
+    constexpr int HALF_W = W_IN / 2;
+    const bool seam_strip = A.seam && strip == 0;
+    int xbase, o_lo, o_hi;
+    if (!A.seam) {
+        o_lo = strip * A.w_valid;
+        o_hi = min(o_lo + A.w_valid, Nx);
+        xbase = o_lo - 4 * K;
+    } else if (seam_strip) {
+        xbase = Nx - HALF_W;  // writes strip columns [4K, W_IN - 4K), wrapped
+        o_lo = o_hi = 0;
+    } else {
+        o_lo = HALF_W - 4 * K + (strip - 1) * A.w_valid;
+        o_hi = min(o_lo + A.w_valid, Nx - HALF_W + 4 * K);
+        xbase = min(o_lo - 4 * K, Nx - W_IN);
+    }
     const int xb = wrapi(xbase, Nx);
     const bool nowrap = xbase >= 0 && xbase + W_IN <= Nx;
+    // the seam strip's shared rows hold its two halves swapped (see SweepMaps):
+    // strip column c sits at c ^ 128, i.e. lane l's 8 columns at lane l ^ 16's
+    const int sl = seam_strip ? lane ^ (HALF_W / LANE_COLS) : lane;
+    const int scx = seam_strip ? HALF_W : 0;
     const int F0 = yb - 4 * K;                // first row fed to level 0
     const int nit = (ye - yb + 8 * K + R - 1) / R + K - 1;
 
@@ -516,14 +547,22 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
     uint64_t *const tbar = reinterpret_cast<uint64_t *>(smem_raw + L::BAR_OFF);
     bool use_tma = false;
     if constexpr (std::is_same<T, float>::value)
-        use_tma = M != nullptr && nowrap && (xb & 7) == 0 && (tc::smem_addr(smem_raw) & 1023u) == 0;
+        use_tma = M != nullptr && ((nowrap && (xb & 7) == 0) || seam_strip) && (tc::smem_addr(smem_raw) & 1023u) == 0;
     uint32_t tph_x = 0, tph_y = 0;
     constexpr uint32_t SROW = W_IN * sizeof(T), CROW = W_IN * sizeof(T2);
     // the R rows of a block (level j) of one pair plane: one box, or R one-row
     // boxes where the block wraps around y
     auto tma_block = [&](void *dst, int j, int it, int plane, uint64_t *bar) {
         const int r0 = growof(j, it, 0);
-        if (r0 + R <= Ny) {
+        if (seam_strip) {
+            if (r0 + R <= Ny) {
+                tma_box5(dst, &M->seam_coef_r, 0, 0, r0, plane, bar);
+            } else {
+                for (int ir = 0; ir < R; ++ir)
+                    tma_box5(static_cast<unsigned char *>(dst) + ir * CROW, &M->seam_coef, 0, 0, growof(j, it, ir),
+                             plane, bar);
+            }
+        } else if (r0 + R <= Ny) {
             tma_row(dst, &M->coef_r, xb >> 3, r0, plane, bar);
         } else {
             for (int ir = 0; ir < R; ++ir)
@@ -534,7 +573,7 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
     // the blocks of n adjacent pair planes (stash slots slot0..) for all K
     // levels: one merged box where they neither wrap around y nor straddle a
     // group of R + 4 rows, else one box (or R one-row boxes) per level and plane
-    const bool merge_ok = merged && K > 1;
+    const bool merge_ok = merged && K > 1 && !seam_strip;
     auto tma_planes = [&](bool ystash, int slot0, int n, int it, int plane0, uint64_t *bar) {
         const int r_top = growof(K - 1, it, 0);
         const int b0 = r_top % (R + 4);
@@ -550,7 +589,16 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
     // level-0 state rows: planes p0 .. p0 + n - 1 into buffer slots s0 ..
     auto tma_state = [&](int it, int half, int p0, int n, int s0, uint64_t *bar) {
         const int r0 = growof(0, it, 0);
-        if (r0 + R <= Ny) {
+        if (seam_strip) {
+            if (r0 + R <= Ny) {
+                const CUtensorMap *map = n == 3 ? &M->seam_state_r3 : (n == 2 ? &M->seam_state_r2 : &M->seam_state_r1);
+                tma_box5(bufrow(0, half, s0, 0), map, 0, 0, r0, p0, bar);
+            } else {
+                for (int q = 0; q < n; ++q)
+                    for (int ir = 0; ir < R; ++ir)
+                        tma_box5(bufrow(0, half, s0 + q, ir), &M->seam_state, 0, 0, growof(0, it, ir), p0 + q, bar);
+            }
+        } else if (r0 + R <= Ny) {
             const CUtensorMap *map = n == 3 ? &M->state_r3 : (n == 2 ? &M->state_r2 : &M->state_r1);
             tma_row(bufrow(0, half, s0, 0), map, xb >> 3, r0, p0, bar);
         } else {
@@ -606,13 +654,14 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
         const int task = tid + u * NT;
         yj[u] = task / W_IN;
         const int c = task % W_IN;
-        st_base[u] = buf + yj[u] * LVL + swz<T>(c);
-        ys_base[u] = yst + (K - 1 - yj[u]) * R * W_IN + swz<T2>(c);
+        st_base[u] = buf + yj[u] * LVL + swz<T>(c ^ scx);
+        ys_base[u] = yst + (K - 1 - yj[u]) * R * W_IN + swz<T2>(c ^ scx);
     }
     const int c_last = (tid + (NY - 1) * NT) % W_IN;
     const bool last_is_final = yj[NY - 1] == K - 1;  // uniform per warp
-    const bool col_ok = c_last >= 4 * K && c_last < 4 * K + A.w_valid && xs0 + (c_last - 4 * K) < Nx;
-    const int gx = xs0 - 4 * K + c_last;
+    const int gcol = xbase + c_last;
+    const bool col_ok = seam_strip ? (c_last >= 4 * K && c_last < W_IN - 4 * K) : (gcol >= o_lo && gcol < o_hi);
+    const int gx = gcol >= Nx ? gcol - Nx : gcol;
     T *const qo_h = qout + size_t(Fm::H) * P + gx;
     T *const qo_px = qout + size_t(Fm::PX) * P + gx;
     T *const qo_py = qout + size_t(Fm::PY) * P + gx;
@@ -663,9 +712,9 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
             T *rh = bufrow(j, cur, Fm::SH, ir);
             T *rp = bufrow(j, cur, Fm::SPX, ir);
             T m[LANE_COLS], s[LANE_COLS], h[LANE_COLS], p[LANE_COLS];
-            sload8pair(m, s, xstrow(j, XS_C, ir), lane);
-            sload8(h, rh, lane);
-            sload8(p, rp, lane);
+            sload8pair(m, s, xstrow(j, XS_C, ir), sl);
+            sload8(h, rh, sl);
+            sload8(p, rp, sl);
             constexpr int SG = Fm::SGX;
             // ops 1-8
 #pragma unroll
@@ -688,7 +737,7 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
             T vc[LANE_COLS], vs[LANE_COLS];
             bool vx_on = false;
             if constexpr (INTER) {
-                sload8pair(vc, vs, xstrow(j, XS_V, ir), lane);
+                sload8pair(vc, vs, xstrow(j, XS_V, ir), sl);
                 unsigned nz = 0;
 #pragma unroll
                 for (int c = 0; c < LANE_COLS; ++c) nz |= nzbits(vc[c]) | nzbits(vs[c]);
@@ -719,8 +768,8 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
                         vop_pair<Fm::TX, Fm::VX_HUB, UNIT>(h[c], p[c], vs[c], vc[c]);
                 }
             }
-            sstore8(rh, lane, h);
-            sstore8(rp, lane, p);
+            sstore8(rh, sl, h);
+            sstore8(rp, sl, p);
             if (use_tma && j == 0) tc::fence_proxy_async();  // level-0 rows are TMA targets again later
         }
         if (use_tma) {
@@ -962,6 +1011,30 @@ inline bool make_sweep_maps(const SweepArgs &a, int K, int R, SweepMaps &m, int 
         };
         *merged = (merged_map(&m.coef_m1, 1) && merged_map(&m.coef_m2, 2)) ? 1 : 0;
     }
+    if (a.seam) {
+        if (a.Nx < W_IN) return false;
+        const cuuint64_t half = cuuint64_t(W_IN / 2);
+        const cuuint64_t hdim[5] = {8, half / 8, 2, Ny, 6};
+        const cuuint64_t hstr[4] = {32, (Nx - half) * 4, Nx * 4, Nx * Ny * 4};
+        auto seam_state = [&](CUtensorMap *map, cuuint32_t rows, cuuint32_t comps) {
+            const cuuint32_t box[5] = {8, cuuint32_t(half / 8), 2, rows, comps};
+            return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(a.q_in), hdim, hstr, box, one,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        if (!seam_state(&m.seam_state, 1, 1) || !seam_state(&m.seam_state_r1, cuuint32_t(R), 1) ||
+            !seam_state(&m.seam_state_r2, cuuint32_t(R), 2) || !seam_state(&m.seam_state_r3, cuuint32_t(R), 3))
+            return false;
+        const cuuint64_t hcdim[5] = {16, half / 8, 2, Ny, cuuint64_t(NPAIR)};
+        const cuuint64_t hcstr[4] = {64, (Nx - half) * 8, Nx * 8, Nx * Ny * 8};
+        auto seam_coef = [&](CUtensorMap *map, cuuint32_t rows) {
+            const cuuint32_t box[5] = {16, cuuint32_t(half / 8), 2, rows, 1};
+            return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void *>(a.coef), hcdim, hcstr, box, one,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        if (!seam_coef(&m.seam_coef, 1) || !seam_coef(&m.seam_coef_r, cuuint32_t(R))) return false;
+    }
     return true;
 }
 
@@ -996,15 +1069,22 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     SweepParams prm;
     memset(&prm, 0, sizeof(prm));
     prm.a = a;
+    // strips: the seam layout wherever the pass copies with TMA
+    prm.split = make_sweep_split(a.Nx, a.Ny, K, R, std::is_same<T, float>::value && a.error != nullptr);
+    prm.a.seam = prm.split.seam;
     if constexpr (std::is_same<T, float>::value)
-        prm.tma = (a.error != nullptr && make_sweep_maps(a, K, R, prm.m, &prm.merged)) ? 1 : 0;
-    const int nsx = (a.Nx + a.w_valid - 1) / a.w_valid;
+        prm.tma = (a.error != nullptr && make_sweep_maps(prm.a, K, R, prm.m, &prm.merged)) ? 1 : 0;
+    if (!prm.tma && prm.split.seam) {  // no tensor maps: every strip copies with cp.async
+        prm.split = make_sweep_split(a.Nx, a.Ny, K, R, 0);
+        prm.a.seam = 0;
+    }
+    const int nsx = prm.split.nsx;
+    if ((long long)nsx * a.Ny >= (1LL << 31)) return cudaErrorInvalidValue;
     if (a.chunk <= 0) {
         // balanced: a.ctas CTAs per family (one per resident slot), each one
         // equal share of its family's rows: no tail wave, and the warm-up
         // rows once per share and strip instead of once per tile
-        prm.split = make_sweep_split(a.Nx, a.Ny, K, R, std::is_same<T, float>::value ? 1 : 0);
-        if (a.ctas < 1 || (long long)prm.split.nsx * a.Ny >= (1LL << 31)) return cudaErrorInvalidValue;
+        if (a.ctas < 1) return cudaErrorInvalidValue;
         sweep_kernel<T, K, R, NY, INTER, UNIT><<<dim3(unsigned(a.ctas), 1, nfam), Cfg::NT, L::SMEM, st>>>(prm);
         return cudaGetLastError();
     }

@@ -116,6 +116,23 @@ def test_fp32_tma_block_boxes_match_oracle(K, Ny, chunk):
     assert rel_l2(got, ref) < 3e-6
 
 
+@pytest.mark.parametrize("Nx, Ny, chunk, K", [(256, 40, 0, 2), (264, 30, 0, 2), (512, 37, 0, 4), (744, 50, 16, 2),
+                                              (2048, 21, 0, 2), (496, 64, 24, 4)])
+@pytest.mark.parametrize("sequence", ["interleaved", "plain"])
+def test_fp32_seam_layout_matches_oracle(Nx, Ny, chunk, K, sequence):
+    """FP32, Nx a multiple of 8 and at least 256, K >= 2: strip 0 straddles
+    the periodic seam and loads its two 128-column halves with one TMA box
+    each (landing swapped in shared memory); the last strip's input is moved
+    left to end at Nx. Cases: Nx = 256 (the seam strip and one strip over 16
+    columns), a last strip clamped against the right edge, Ny not a multiple
+    of R (boxes at the y-wrap loaded row by row), tiles and the balanced split."""
+    n, q0 = problem(Nx, Ny, seed=13)
+    delta, steps = 0.2, 3 * K + 1
+    got = gpu_run(n, q0, delta, steps, precision="fp32", steps_per_pass=K, chunk_rows=chunk, sequence=sequence)
+    ref = oracle_run(n, q0, delta, steps, sequence, "paper")
+    assert rel_l2(got, ref) < 3e-6
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("Nx, Ny", [(1000, 777), (2048, 300)])
 def test_balanced_split_equals_tiles_bit_exact(precision, Nx, Ny):
@@ -135,7 +152,7 @@ def test_balanced_split_covers_the_units():
     n, q0 = problem(2048, 300, seed=2)
     with Simulation(*n, 0.2, precision="fp32", steps_per_pass=2) as sim:
         b = sim.sweep_split()
-        nsx = -(-2048 // 240)
+        nsx = 1 + -(-(2048 - 256 + 16) // 240)  # the seam strip and the strips between
         assert b is not None and b[0] == 0 and b[-1] == nsx * 300 and np.all(np.diff(b) >= 0)
         assert b.size - 1 <= nsx * 300
     with Simulation(*n, 0.2, precision="fp32", steps_per_pass=2, chunk_rows=64) as sim:
@@ -316,12 +333,14 @@ def window(a, yc, xc, H):
 def share_seams(sim, Ny, shares, W=240):
     """(row, column) sites on the seam between share b - 1 and share b of the
     balanced split, for each b in shares: the first row of share b, in the
-    middle of its strip's columns."""
+    middle of its strip's columns. Seam layout at 2 steps per pass: strip 0
+    writes columns [Nx - 120, Nx) and [0, 120), strip s >= 1 the W = 240
+    columns from 120 + (s - 1) W, so strip s is centred on column s W."""
     bounds = sim.sweep_split()
     out = []
     for b in shares:
         s, y = divmod(int(bounds[b]), Ny)
-        out.append((y, s * W + W // 2))
+        out.append((y, s * W))
     return out
 
 
@@ -337,12 +356,14 @@ def test_cylinders_8192_sampled_parity():
         sim.step(steps)
         got = sim.get_fields(dtype=np.float32)
     H = 4 * steps + 8
-    # sample sites: pulse flank, object edges, lattice corners (periodic wrap),
-    # strip seams (240 written columns per strip) and the seams between the
-    # CTA shares of the balanced split (rows where one CTA's share ends)
+    # sample sites: pulse flank, object edges, lattice corners (periodic wrap,
+    # inside the seam strip), strip seams (strip s >= 1 writes the 240 columns
+    # from 120 + 240 (s - 1); the seam strip the 120 either side of x = 0) and
+    # the seams between the CTA shares of the balanced split
     obj = w.objects[0]
     samples = [(4096, 1024 + 100), (0, 0), (8191, 8191), (int(obj.cy), int(obj.cx - obj.a)),
-               (int(obj.cy + obj.b), int(obj.cx)), (1234, 240), (4096, 239), (8000, 8180)] + seams
+               (int(obj.cy + obj.b), int(obj.cx)), (1234, 360), (4096, 359), (8000, 8180), (5000, 8072),
+               (6000, 119)] + seams
     for yc, xc in samples:
         nw = tuple(window(a, yc, xc, H) for a in n)
         qw = window(q0, yc, xc, H)
@@ -374,9 +395,9 @@ def test_cylinders_8192_sampled_parity_200_steps():
     H = 4 * steps + 8
     x0 = int(w.pulse.x0)
     # a share seam inside the pulse's strip: the first share that starts in it below row 4096
-    strip = (x0 - 40) // 240
+    strip = (x0 - 40 + 120) // 240  # seam layout (see share_seams)
     seam = next(int(u) % 8192 for u in bounds if int(u) // 8192 == strip and int(u) % 8192 > 4096)
-    samples = [(4096, x0 + 60), (seam, x0 - 40), (3000, 960), (0, x0 + 10), (8191, x0 - 120)]
+    samples = [(4096, x0 + 60), (seam, x0 - 40), (3000, 1080), (0, x0 + 10), (8191, x0 - 120)]
     for yc, xc in samples:
         nw = tuple(window(a, yc, xc, H) for a in n)
         qw = window(q0, yc, xc, H)

@@ -1,13 +1,16 @@
-"""Host-side checks of the balanced split of a sweep pass (qla_sweep_split).
+"""Host-side checks of the strips and balanced split of a sweep pass
+(qla_sweep_split).
 
 With chunk_rows = 0 a pass launches one CTA per resident slot and family;
 CTA b sweeps the row units [bounds[b], bounds[b + 1]) (u = strip * Ny + y) as
 one segment per strip it touches. The bounds come from the library's host
 arithmetic, the same code the kernel runs per CTA. These tests check, with no
-GPU visible, that the shares tile the units exactly and that their costs
-under the documented model agree: 16 per row of a strip copied by TMA, more
-per row of an FP32 strip that wraps around x (copied with cp.async), and the
-warm-up rows 8K + R (K - 1) at each strip start.
+GPU visible, the strip count of both layouts (FP32 with K >= 2, Nx a multiple
+of 8 and at least 256: strip 0 straddles the periodic seam and strips of
+256 - 8K outputs cover the columns between; otherwise strips of 256 - 8K
+outputs from column 0), that the shares tile the units exactly, and that
+their costs (one per row, plus the warm-up rows 8K + R (K - 1) at each strip
+start) agree within one strip start's warm-up.
 """
 import numpy as np
 import pytest
@@ -26,31 +29,23 @@ def built():
 
 
 def model(Nx, Ny, K, precision):
-    """Per-strip row costs and the warm-up rows of the documented model. The
-    slow-strip weights (32 at K = 1, 2; 26 at K = 4) are the library's
-    measured constants."""
+    """Strip count and warm-up rows of the documented layout."""
     wv = W_IN - 8 * K
-    nsx = -(-Nx // wv)
     R = 8 if (precision == "fp32" and K == 1) else 4
-    tma_ok = precision == "fp32" and Nx % 8 == 0
-    w = []
-    for s in range(nsx):
-        xbase = s * wv - 4 * K
-        uses_tma = tma_ok and xbase >= 0 and xbase + W_IN <= Nx and xbase % 8 == 0
-        w.append(16 if (uses_tma or not tma_ok) else (26 if K >= 4 else 32))
-    return nsx, w, 8 * K + R * (K - 1)
+    seam = precision == "fp32" and Nx % 8 == 0 and Nx >= W_IN and K >= 2
+    nsx = 1 + -(-(Nx - W_IN + 8 * K) // wv) if seam else -(-Nx // wv)
+    return nsx, 8 * K + R * (K - 1)
 
 
-def share_costs(b, Ny, w, warm):
-    """Cost of each share: its rows at their strip's row cost, plus the warm-up
-    of every strip start it holds."""
+def share_costs(b, Ny, warm):
+    """Cost of each share: its rows, plus the warm-up of every strip start it holds."""
     costs = []
     for u0, u1 in zip(b[:-1], b[1:]):
-        c, u = 0, u0
+        c, u = 0, int(u0)
         while u < u1:
-            s, y0 = divmod(int(u), Ny)
+            s, y0 = divmod(u, Ny)
             y1 = min(Ny, y0 + int(u1 - u))
-            c += w[s] * (y1 - y0) + (16 * warm if y0 == 0 else 0)
+            c += (y1 - y0) + (warm if y0 == 0 else 0)
             u += y1 - y0
         costs.append(c)
     return np.array(costs)
@@ -59,29 +54,29 @@ def share_costs(b, Ny, w, warm):
 @pytest.mark.parametrize("Nx,Ny,K,G,precision", [(8192, 8192, 2, 304, "fp32"), (4096, 4096, 4, 152, "fp32"),
                                                  (1024, 1024, 4, 152, "fp32"), (1000, 777, 2, 304, "fp32"),
                                                  (8192, 8192, 2, 304, "fp64"), (300, 40, 1, 152, "fp32"),
-                                                 (240, 3, 2, 5, "fp32"), (7, 5, 2, 1, "fp64")])
+                                                 (240, 3, 2, 5, "fp32"), (7, 5, 2, 1, "fp64"),
+                                                 (256, 64, 2, 304, "fp32"), (1004, 50, 2, 40, "fp32")])
 def test_shares_tile_the_units_with_equal_cost(Nx, Ny, K, G, precision):
     b = qla.sweep_split(Nx, Ny, K, G, precision)
-    nsx, w, warm = model(Nx, Ny, K, precision)
+    nsx, warm = model(Nx, Ny, K, precision)
     assert b.size == G + 1 and b[0] == 0 and b[-1] == nsx * Ny and np.all(np.diff(b) >= 0)
-    costs = share_costs(b, Ny, w, warm)
-    total = sum(16 * warm + w[s] * Ny for s in range(nsx))
+    costs = share_costs(b, Ny, warm)
+    total = nsx * (Ny + warm)
     assert costs.sum() == total
-    # a bound lands on the first unit whose cost prefix reaches its ideal
-    # position: off by less than one row's cost, or by a strip's warm-up
-    slack = max(w) + 16 * warm
-    assert np.all(np.abs(costs - total / G) <= 2 * slack), (costs.min(), costs.max(), total / G)
+    # a bound lands where its ideal cost position falls, except inside a
+    # strip's warm-up, where it moves to the strip's first row
+    assert np.all(np.abs(costs - total / G) <= warm + 1), (costs.min(), costs.max(), total / G)
 
 
-def test_slow_strips_are_the_ones_that_wrap():
-    # 8192 columns at K = 2: strips of 240 outputs; strip 0 starts at column
-    # -8 and strip 34 ends past 8192, so both copy with cp.async
-    nsx, w, _ = model(8192, 8192, 2, "fp32")
-    assert nsx == 35 and w[0] == w[34] == 32 and all(x == 16 for x in w[1:34])
-    b = qla.sweep_split(8192, 8192, 2, 304)
-    first = b[1] - b[0]
-    mid = np.median(np.diff(b))
-    assert first < 0.6 * mid  # a slow strip's share holds about half the rows
+def test_seam_layout_strip_count():
+    # 8192 columns at K = 2: the seam strip writes [8072, 8192) and [0, 120);
+    # 34 strips of 240 cover the 7952 columns between
+    assert model(8192, 8192, 2, "fp32")[0] == 35
+    assert qla.sweep_split(8192, 8192, 2, 1)[-1] == 35 * 8192
+    # the plain layout: 8192 / 240 -> 35 strips as well; 1000 columns (not a
+    # multiple of 8) -> 5 strips; 1000 + 4 -> seam strip + 4
+    assert qla.sweep_split(1000, 10, 2, 1)[-1] == 5 * 10
+    assert qla.sweep_split(1004, 10, 2, 1)[-1] == (1 + 4) * 10
 
 
 def test_rejects_bad_arguments():
