@@ -259,22 +259,30 @@ qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_ro
  * lattice is cut into strips of 256 - 8K output columns (K = steps_per_pass;
  * a strip reads 256 columns, its halo included); in FP32 with K >= 2 and Nx a
  * multiple of 8, at least 256, strip 0 straddles the periodic seam x = 0 and
- * strips 1.. cover the columns between. Row unit u = strip * Ny + y. Each of
- * `ctas` CTAs per family sweeps the units [bounds[b], bounds[b + 1]) of equal
- * cost (one per row, plus the 8K + R (K - 1) warm-up rows, R = 4 (8 for FP32
- * at K = 1), at each strip start).
- * bounds: caller-owned, capacity >= ctas + 1 entries; bounds[0] = 0 and
- * bounds[ctas] = strips * Ny. Host arithmetic only: needs no GPU.
- * QLA_EINVAL on a bad size, precision, CTA count or capacity;
- * QLA_EUNSUPPORTED if steps_per_pass is not instantiated for the precision. */
-qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, long long *bounds,
-                           int capacity);
+ * strips 1.. cover the columns between. Row unit u = strip * Ny + y. The
+ * `ctas` CTAs of a family's layer sweep the units [bounds[b], bounds[b + 1])
+ * (share b). Shares are sized by estimated cost: one per row (the seam
+ * strip's rows a little more), plus the 8K + R (K - 1) warm-up rows, R = 4
+ * (8 for FP32 at K = 1), at each strip start, and weighted by the CTAs' start
+ * (with one layer, or in the first of two: the first ctas/2 CTAs, the first
+ * resident on their SMs, a few percent more; in the second of two layers,
+ * where the CTAs start as the first layer's finish, decreasing with the order
+ * of start, share b going to the b-th CTA to start).
+ * family: QLA_FAMILY_TM or QLA_FAMILY_TE; layers: 1 (one family advanced) or
+ * 2 (both: TM is the first layer). bounds: caller-owned, capacity >= ctas + 1
+ * entries; bounds[0] = 0 and bounds[ctas] = strips * Ny. Host arithmetic only:
+ * needs no GPU. QLA_EINVAL on a bad size, precision, family, layer count, CTA
+ * count or capacity; QLA_EUNSUPPORTED if steps_per_pass is not instantiated
+ * for the precision. */
+qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, int family, int layers,
+                           long long *bounds, int capacity);
 
-/* The split the context's passes of steps_per_pass steps use: *ctas = CTAs
- * per family (0 when the context sweeps tiles of chunk_rows rows instead),
- * and, if bounds is not NULL and *ctas > 0, the share bounds as
- * qla_sweep_split writes them (capacity >= *ctas + 1). */
-qla_status qla_get_sweep_split(const qla_ctx *ctx, int steps_per_pass, int *ctas, long long *bounds,
+/* The split the context's passes of steps_per_pass steps use for `family`:
+ * *ctas = CTAs of the family's layer (0 when the context sweeps tiles of
+ * chunk_rows rows instead, or does not advance the family), and, if bounds is
+ * not NULL and *ctas > 0, the share bounds as qla_sweep_split writes them
+ * (capacity >= *ctas + 1). */
+qla_status qla_get_sweep_split(const qla_ctx *ctx, int steps_per_pass, int family, int *ctas, long long *bounds,
                                int capacity);
 
 /* Text of the last error on the context (empty string if none). */

@@ -28,6 +28,7 @@ struct qla_ctx {
     qla::DiagResult *diag_dev = nullptr;
     qla::DiagResult *diag_host = nullptr;
     int *sweep_err = nullptr;       // device flag: a bounded wait of the sweep's TMA copies ran out
+    unsigned *share_order = nullptr;  // device counter: start order of the balanced split's last layer
     int *sweep_err_host = nullptr;  // pinned
     size_t esize = 4;
     int K = 4;
@@ -137,6 +138,7 @@ qla_status launch_pass(qla_ctx *c, int K) {
     a.w_valid = qla::sweep_strip_width() - 8 * K;
     a.chunk = c->chunk;
     a.ctas = c->ctas[K];
+    a.order = c->share_order;
     a.interleaved = c->opt.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0;
     a.unitary = c->opt.potential == QLA_POT_UNITARY ? 1 : 0;
     a.vec = (c->Nx % int(16 / c->esize)) == 0 ? 1 : 0;
@@ -199,7 +201,7 @@ qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_bu
     out->coeff_bytes = round_up(size_t(qla::NCOEF) * P * es, kAlign);
     out->index_bytes = round_up(3 * P * sizeof(double), kAlign);
     out->scratch_bytes = round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign) + round_up(sizeof(qla::DiagResult), kAlign) +
-                         kAlign;  // sweep error flag
+                         kAlign;  // sweep error flag, share-order counter
     return QLA_OK;
 }
 
@@ -278,7 +280,9 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
     if (cudaMallocHost(reinterpret_cast<void **>(&c->diag_host), sizeof(qla::DiagResult)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void **>(&c->sweep_err_host), sizeof(int)) != cudaSuccess)
         return bail(QLA_ENOMEM);
-    if (cudaMemsetAsync(c->sweep_err, 0, sizeof(int), c->stream) != cudaSuccess) return bail(QLA_ECUDA);
+    // the sweep error flag and, 64 bytes on in the same slot, the share-order counter
+    c->share_order = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(c->sweep_err) + 64);
+    if (cudaMemsetAsync(c->sweep_err, 0, kAlign, c->stream) != cudaSuccess) return bail(QLA_ECUDA);
     for (int k = 0; k < 3; ++k)
         if (cudaMemcpyAsync(c->index + size_t(k) * P, nn[k], P * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream) != cudaSuccess)
@@ -518,23 +522,29 @@ qla_status write_split(const qla::SweepSplit &sp, int ctas, long long *bounds, i
 }
 }  // namespace
 
-qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, long long *bounds,
-                           int capacity) {
+qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, int family, int layers,
+                           long long *bounds, int capacity) {
     if (Nx < 1 || Ny < 1 || (precision != QLA_FP32 && precision != QLA_FP64)) return QLA_EINVAL;
+    if ((family != QLA_FAMILY_TM && family != QLA_FAMILY_TE) || (layers != 1 && layers != 2)) return QLA_EINVAL;
     if (!qla::sweep_supported(precision, steps_per_pass)) return QLA_EUNSUPPORTED;
     const int prec = precision == QLA_FP64 ? 1 : 0;
-    const qla::SweepSplit sp =
-        qla::make_sweep_split(Nx, Ny, steps_per_pass, qla::sweep_block_rows(prec, steps_per_pass), prec ? 0 : 1);
+    const int fam = family == QLA_FAMILY_TE ? 1 : 0;
+    const qla::SweepSplit sp = qla::make_sweep_split(Nx, Ny, steps_per_pass, qla::sweep_block_rows(prec, steps_per_pass),
+                                                     prec ? 0 : 1, fam, layers == 2 ? fam : 0, layers);
     if ((long long)sp.nsx * Ny >= (1LL << 31)) return QLA_EINVAL;
     return write_split(sp, ctas, bounds, capacity);
 }
 
-qla_status qla_get_sweep_split(const qla_ctx *c, int steps_per_pass, int *ctas, long long *bounds, int capacity) {
+qla_status qla_get_sweep_split(const qla_ctx *c, int steps_per_pass, int family, int *ctas, long long *bounds,
+                               int capacity) {
     if (!c || !ctas) return QLA_EINVAL;
+    if (family != QLA_FAMILY_TM && family != QLA_FAMILY_TE) return QLA_EINVAL;
     if (!qla::sweep_supported(c->opt.precision, steps_per_pass)) return QLA_EUNSUPPORTED;
-    *ctas = c->chunk > 0 ? 0 : c->ctas[steps_per_pass];
+    const bool advanced = c->opt.families == QLA_FAMILIES_BOTH || c->opt.families == family;
+    *ctas = c->chunk > 0 || !advanced ? 0 : c->ctas[steps_per_pass];
     if (*ctas == 0 || !bounds) return QLA_OK;
-    return qla_sweep_split(c->Nx, c->Ny, c->opt.precision, steps_per_pass, *ctas, bounds, capacity);
+    return qla_sweep_split(c->Nx, c->Ny, c->opt.precision, steps_per_pass, *ctas, family,
+                           c->opt.families == QLA_FAMILIES_BOTH ? 2 : 1, bounds, capacity);
 }
 
 const char *qla_last_error(const qla_ctx *c) { return c ? c->msg.c_str() : "NULL context"; }

@@ -46,38 +46,75 @@ struct Family {
 };
 
 // Strips and balanced split of a pass. The row units u = strip * Ny + y of
-// a family (nsx strips, Ny rows each) are shared among the CTAs of the
-// family's grid layer in equal shares of cost; a CTA sweeps its units as one
-// segment per strip it touches. Cost, in rows: one per row, plus `warm` at
-// each strip's start (the warm-up rows a segment that starts there sweeps in
-// addition). Every strip of a pass costs the same per row: with the seam
-// layout all of them copy with TMA, and without it (FP64; FP32 with K = 1, Nx
-// not a multiple of 8, or Nx < W_IN) none does.
+// a family (nsx strips, Ny rows each) are shared among the G CTAs of the
+// family's grid layer in shares of estimated cost; a CTA sweeps its units as
+// one segment per strip it touches. Cost, in sixteenths of a row: 16 per row
+// (w_seam per row of the seam strip, which issues more TMA copies: its state
+// and coefficient boxes are two-half views and its coefficient levels come in
+// separate boxes) and 16 * warm at each strip's start (the warm-up rows a
+// segment that starts there sweeps in addition). Without the seam layout
+// (FP64; FP32 with K = 1, Nx not a multiple of 8, or Nx < W_IN) no strip copies
+// with TMA and every row costs the same. Share sizes (profile):
+//   0: equal;
+//   1: (G even) shares b < G/2 larger by p64/64 and the others smaller by as
+//      much: the first G/2 CTAs of a launch are the first on their SMs, and
+//      the warp schedulers favour the older of two resident CTAs;
+//   2: decreasing linearly from 1 + p64/64 to 1 - p64/64 times the mean, taken
+//      in the order the CTAs start (the last family layer of a launch: its
+//      CTAs start as the previous layer's finish, over a spread of times).
 struct SweepSplit {
     int Nx, Ny;
     int w_valid;  // output columns per strip
     int nsx;      // strips
     int warm;     // warm-up rows of a segment: 8K + R (K - 1)
     int seam;     // the seam layout (SweepArgs::seam)
+    int w_seam;   // cost of a row of the seam strip (sixteenths)
+    int profile;  // share sizes (above)
+    int p64;
 
-    __host__ __device__ long long cost_total() const { return (long long)nsx * (Ny + warm); }
+    __host__ __device__ long long strip0_cost() const {
+        return 16LL * warm + (long long)(seam ? w_seam : 16) * Ny;
+    }
+    __host__ __device__ long long cost_total() const {
+        return strip0_cost() + (long long)(nsx - 1) * 16 * (Ny + warm);
+    }
     // The row unit at cost position c (0 <= c <= cost_total(); a position
     // inside a strip's warm-up maps to the strip's first row): monotonic, so
-    // the shares [unit(C b / G), unit(C (b + 1) / G)), b = 0 .. G - 1, tile the
-    // nsx * Ny units exactly.
+    // shares [unit(c_b), unit(c_{b+1})) for increasing c_b tile the nsx * Ny
+    // units exactly.
     __host__ __device__ long long unit_of_cost(long long c) const {
-        const long long per = Ny + warm;
-        const long long s = c / per;
+        const long long c0 = strip0_cost();
+        if (c < c0) {
+            const long long r = c - 16LL * warm;
+            return r <= 0 ? 0 : r / (seam ? w_seam : 16);
+        }
+        const long long per = 16LL * (Ny + warm);
+        const long long s = 1 + (c - c0) / per;
         if (s >= nsx) return (long long)nsx * Ny;
-        const long long r = c - s * per - warm;  // rows of strip s covered
-        return s * Ny + (r <= 0 ? 0 : r);
+        const long long r = c - c0 - (s - 1) * per - 16LL * warm;  // cost into strip s's rows
+        return s * Ny + (r <= 0 ? 0 : r / 16);
     }
-    __host__ __device__ long long share_begin(int b, int G) const { return unit_of_cost(cost_total() * b / G); }
+    // Cost position where share b of G begins (the profile's weights summed
+    // over the shares before b, as a fraction num / den of the total).
+    __host__ __device__ long long share_begin(int b, int G) const {
+        long long num = b, den = G;
+        if (profile == 1 && G % 2 == 0 && G <= 4096) {
+            const long long H = G / 2;
+            num = b <= H ? b * (64LL + p64) : H * (64LL + p64) + (b - H) * (64LL - p64);
+            den = 64LL * G;
+        } else if (profile == 2 && G >= 2 && G <= 4096) {
+            num = 64LL * (G - 1) * b + (long long)p64 * b * (G - b);
+            den = 64LL * G * (G - 1);
+        }
+        return unit_of_cost(cost_total() / den * num + cost_total() % den * num / den);
+    }
 };
 
-// The strips and split of a pass of K steps (R rows per iteration) over an
-// Nx x Ny lattice; tma: the pass may copy with TMA (FP32 with its tensor maps).
-SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma);
+// The strips and split of one family layer of a pass of K steps (R rows per
+// iteration) over an Nx x Ny lattice; tma: the pass may copy with TMA (FP32
+// with its tensor maps); fam: the layer's family (0 = TM, 1 = TE); layer,
+// layers: the layer's index and the pass's number of family layers (1, 2).
+SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma, int fam = 0, int layer = 0, int layers = 1);
 // Rows per iteration R of the sweep instantiated for (precision, K).
 int sweep_block_rows(int precision, int K);
 
@@ -97,6 +134,10 @@ struct SweepArgs {
     // strip s from column W_IN/2 - 4K + (s - 1) w_valid, the last one's input
     // moved left to end at Nx at the latest (it writes only its own columns).
     int seam;
+    // Balanced split, last of two family layers: a counter (zero between
+    // launches) from which the layer's CTAs take their share index in the
+    // order they start; null: share = blockIdx.x.
+    unsigned *order;
     int interleaved;    // 1: Eq. 28, 0: Eq. 23
     int unitary;        // 1: unitary potentials
     int vec;            // 1: 16-byte vector access is legal (Nx multiple of 16/sizeof(T))

@@ -92,7 +92,7 @@ struct SweepParams {
     int tma;
     int merged;
     int tiles_fastest;  // grid x runs over the row tiles of a strip (else over the strips of a tile row)
-    SweepSplit split;  // balanced split (a.chunk == 0)
+    SweepSplit split[2];  // per family layer (blockIdx.z): strips and balanced split (a.chunk == 0)
 };
 
 template <typename T>
@@ -390,7 +390,8 @@ struct SweepLayout {
     static constexpr size_t YST = size_t(K) * NYS * R * W_IN * sizeof(T2);
     static constexpr size_t XST = size_t(K) * NXS * R * W_IN * sizeof(T2);
     static constexpr size_t BAR_OFF = STATE + YST + XST;  // mbarriers of the two TMA copy groups
-    static constexpr size_t SMEM = BAR_OFF + 16;
+    static constexpr size_t ORD_OFF = BAR_OFF + 16;       // the CTA's share index (start order)
+    static constexpr size_t SMEM = ORD_OFF + 16;
 };
 
 template <typename T, int K, int R, int NY>
@@ -929,8 +930,20 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
     const int Ny = prm.a.Ny;
     int u, u1;  // this CTA's row units [u, u1) (nsx * Ny < 2^31, checked on the host)
     if (prm.a.chunk <= 0) {
-        u = int(prm.split.share_begin(blockIdx.x, gridDim.x));
-        u1 = int(prm.split.share_begin(blockIdx.x + 1, gridDim.x));
+        const SweepSplit &sp = prm.split[blockIdx.z];
+        int b = blockIdx.x;
+        if (sp.profile == 2 && prm.a.order) {  // share index = start order
+            int *const ord = reinterpret_cast<int *>(smem_raw + SweepLayout<T, K, R, INTER>::ORD_OFF);
+            if (threadIdx.x == 0) {
+                const unsigned k = atomicAdd(prm.a.order, 1u);
+                if (k + 1 == gridDim.x) atomicExch(prm.a.order, 0u);  // the last to start: zero for the next launch
+                *ord = int(k % gridDim.x);
+            }
+            __syncthreads();
+            b = *ord;
+        }
+        u = int(sp.share_begin(b, gridDim.x));
+        u1 = int(sp.share_begin(b + 1, gridDim.x));
     } else {
         const int strip = prm.tiles_fastest ? blockIdx.y : blockIdx.x;
         const int chunk = prm.tiles_fastest ? blockIdx.x : blockIdx.y;
@@ -1070,15 +1083,16 @@ cudaError_t launch_sweep_t(const SweepArgs &a, int nfam, cudaStream_t st) {
     memset(&prm, 0, sizeof(prm));
     prm.a = a;
     // strips: the seam layout wherever the pass copies with TMA
-    prm.split = make_sweep_split(a.Nx, a.Ny, K, R, std::is_same<T, float>::value && a.error != nullptr);
-    prm.a.seam = prm.split.seam;
+    const bool try_tma = std::is_same<T, float>::value && a.error != nullptr;
+    for (int z = 0; z < nfam; ++z) prm.split[z] = make_sweep_split(a.Nx, a.Ny, K, R, try_tma, a.fam0 + z, z, nfam);
+    prm.a.seam = prm.split[0].seam;
     if constexpr (std::is_same<T, float>::value)
         prm.tma = (a.error != nullptr && make_sweep_maps(prm.a, K, R, prm.m, &prm.merged)) ? 1 : 0;
-    if (!prm.tma && prm.split.seam) {  // no tensor maps: every strip copies with cp.async
-        prm.split = make_sweep_split(a.Nx, a.Ny, K, R, 0);
+    if (!prm.tma && prm.a.seam) {  // no tensor maps: every strip copies with cp.async
+        for (int z = 0; z < nfam; ++z) prm.split[z] = make_sweep_split(a.Nx, a.Ny, K, R, 0, a.fam0 + z, z, nfam);
         prm.a.seam = 0;
     }
-    const int nsx = prm.split.nsx;
+    const int nsx = prm.split[0].nsx;
     if ((long long)nsx * a.Ny >= (1LL << 31)) return cudaErrorInvalidValue;
     if (a.chunk <= 0) {
         // balanced: a.ctas CTAs per family (one per resident slot), each one

@@ -26,7 +26,16 @@ int sweep_block_rows(int precision, int K) {
     return 4;                                   // FP64 (qla_sweep_f64.cu)
 }
 
-SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma) {
+// Balanced-split weights, measured on GB300 (8192^2, 2 steps per pass, two
+// CTAs per SM; per-CTA start and end times by globaltimer): the seam strip's
+// shares ran 1.10x (TM) and 1.19x (TE) as long per row as the others; the
+// first 152 TM CTAs (one per SM) 731.7 us against 806.9 us for the second
+// 152; the TE CTAs started over 256 us as the TM CTAs finished.
+constexpr int kSeamRowCost[2] = {18, 19};  // sixteenths, TM, TE
+constexpr int kOlderShare64 = 3;           // profile 1
+constexpr int kStartOrderSlope64 = 8;      // profile 2
+
+SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma, int fam, int layer, int layers) {
     SweepSplit s;
     s.Nx = Nx;
     s.Ny = Ny;
@@ -35,6 +44,9 @@ SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma) {
     s.seam = tma && Nx % 8 == 0 && Nx >= W_IN && K >= 2 ? 1 : 0;
     s.nsx = s.seam ? 1 + (Nx - W_IN + 8 * K + s.w_valid - 1) / s.w_valid : (Nx + s.w_valid - 1) / s.w_valid;
     s.warm = 8 * K + R * (K - 1);
+    s.w_seam = kSeamRowCost[fam ? 1 : 0];
+    s.profile = layers == 2 && layer == 1 ? 2 : 1;
+    s.p64 = s.profile == 2 ? kStartOrderSlope64 : kOlderShare64;
     return s;
 }
 

@@ -127,22 +127,24 @@ def load_library(path: str = LIB_PATH):
     L.qla_destroy.restype = None
     L.qla_diagnostics_noalloc.argtypes = [v, i, i, i, v, P(Diag)]
     L.qla_diagnostics_noalloc.restype = st
-    L.qla_sweep_split.argtypes = [i, i, i, i, i, P(ctypes.c_longlong), i]
+    L.qla_sweep_split.argtypes = [i, i, i, i, i, i, i, P(ctypes.c_longlong), i]
     L.qla_sweep_split.restype = st
-    L.qla_get_sweep_split.argtypes = [v, i, P(i), P(ctypes.c_longlong), i]
+    L.qla_get_sweep_split.argtypes = [v, i, i, P(i), P(ctypes.c_longlong), i]
     L.qla_get_sweep_split.restype = st
     _lib = L
     return L
 
 
-def sweep_split(Nx: int, Ny: int, steps_per_pass: int, ctas: int, precision: str = "fp32") -> np.ndarray:
+def sweep_split(Nx: int, Ny: int, steps_per_pass: int, ctas: int, precision: str = "fp32", family: str = "TM",
+                layers: int = 2) -> np.ndarray:
     """Share bounds of the balanced split of an Nx x Ny pass of steps_per_pass
-    steps over `ctas` CTAs per family (host arithmetic of the library; no GPU)."""
+    steps over `ctas` CTAs of a family's layer, in a pass of `layers` family
+    layers (host arithmetic of the library; no GPU)."""
     L = load_library()
     out = np.zeros(int(ctas) + 1, dtype=np.int64)
     st = L.qla_sweep_split(int(Nx), int(Ny), _code("precision", {"fp32": FP32, "fp64": FP64}, precision),
-                           int(steps_per_pass), int(ctas), out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
-                           out.size)
+                           int(steps_per_pass), int(ctas), _code("family", {"TM": FAMILY_TM, "TE": FAMILY_TE}, family),
+                           int(layers), out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), out.size)
     if st != 0:
         raise QLAError(st, "qla_sweep_split")
     return out
@@ -321,18 +323,20 @@ class Simulation:
     def synchronize(self):
         self._check(self._L.qla_synchronize(self._ctx), "qla_synchronize")
 
-    def sweep_split(self, steps_per_pass: Optional[int] = None) -> Optional[np.ndarray]:
-        """Share bounds (row units u = strip * Ny + y, one share per CTA of a
-        family) of the balanced split that passes of steps_per_pass steps use
-        (default: the configured steps per pass); None when the context sweeps
-        fixed tiles of chunk_rows rows."""
+    def sweep_split(self, steps_per_pass: Optional[int] = None, family: str = "TM") -> Optional[np.ndarray]:
+        """Share bounds (row units u = strip * Ny + y, one share per CTA of the
+        family's layer) of the balanced split that passes of steps_per_pass
+        steps use (default: the configured steps per pass); None when the
+        context sweeps fixed tiles of chunk_rows rows or does not advance the
+        family."""
         K = int(steps_per_pass or self.steps_per_pass)
+        fam = _code("family", {"TM": FAMILY_TM, "TE": FAMILY_TE}, family)
         n = ctypes.c_int()
-        self._check(self._L.qla_get_sweep_split(self._ctx, K, ctypes.byref(n), None, 0), "qla_get_sweep_split")
+        self._check(self._L.qla_get_sweep_split(self._ctx, K, fam, ctypes.byref(n), None, 0), "qla_get_sweep_split")
         if n.value == 0:
             return None
         out = np.zeros(n.value + 1, dtype=np.int64)
-        self._check(self._L.qla_get_sweep_split(self._ctx, K, ctypes.byref(n),
+        self._check(self._L.qla_get_sweep_split(self._ctx, K, fam, ctypes.byref(n),
                                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), out.size),
                     "qla_get_sweep_split")
         return out

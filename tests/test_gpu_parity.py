@@ -147,14 +147,18 @@ def test_balanced_split_equals_tiles_bit_exact(precision, Nx, Ny):
 
 
 def test_balanced_split_covers_the_units():
-    """The context's split: one share per resident slot, bounds tiling the
-    strips x rows, and a context with chunk_rows set reports no split."""
+    """The context's split: one share per resident slot (two 112 KB CTAs per
+    SM at 2 steps per pass), bounds tiling the strips x rows, and a context
+    with chunk_rows set reports no split."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     n, q0 = problem(2048, 300, seed=2)
     with Simulation(*n, 0.2, precision="fp32", steps_per_pass=2) as sim:
         b = sim.sweep_split()
         nsx = 1 + -(-(2048 - 256 + 16) // 240)  # the seam strip and the strips between
         assert b is not None and b[0] == 0 and b[-1] == nsx * 300 and np.all(np.diff(b) >= 0)
-        assert b.size - 1 <= nsx * 300
+        assert b.size - 1 == 2 * sms
     with Simulation(*n, 0.2, precision="fp32", steps_per_pass=2, chunk_rows=64) as sim:
         assert sim.sweep_split() is None and sim.chunk_rows == 64
 
