@@ -34,14 +34,15 @@ sys.path.insert(0, ROOT)
 # (one pass) of two sweep launches of this benchmark's own command on the 8192^2 workload
 # (profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
 # excluded), the workload, the steps per pass and the launch form (balanced split) match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "0f839fbf79fbd9bf", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 7.79978e9}
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "431381dc86281234", "workload": "cylinders8192_fp32",
+                    "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 7.77460e9}
 
 L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"
 UNIT = "site-updates/s"
 BYTES_PER_SITE_UPDATE = 60.0  # FP32 general kernel: 24 B state read + 24 B write + 12 B n_x, n_y, n_z
 QLA_STEPS_PER_BENCH_STEP = 100
+E2E_CONTEXTS = 3  # contexts in flight in the pipelined e2e leg
 
 
 def measured_peaks():
@@ -272,14 +273,17 @@ def run_ours(args):
     # e2e through the public API with host buffers: pinned H2D state copy,
     # qla_step, diagnostics, D2H state copy, every bench step. Serial: one
     # context, each step's copies between its compute. Pipelined (the reported
-    # value): two contexts on their own streams, each stepping its own lattice
-    # of the workload, so that one context's host copies overlap the other's
-    # compute (qla_set_fields_f32 and qla_step are asynchronous on the
-    # context's stream; diagnostics and the read-back synchronise it). The
-    # sweeps of the two contexts run one after the other (an event orders
-    # them): each pass of the balanced split is one wave of CTAs sized for
-    # the whole GPU, so two passes sharing the SMs would both run long.
-    e2e_value = e2e_serial = None
+    # value): E2E_CONTEXTS contexts on their own streams, each stepping its own
+    # lattice of the workload, bench step i on context i mod E2E_CONTEXTS, so
+    # that the host copies of one step overlap the compute of the others
+    # (qla_set_fields_f32 and qla_step are asynchronous on the context's
+    # stream; diagnostics and the read-back synchronise it) and a read-back
+    # that the host stalls in (measured on GB300: now and then 25-70 ms for
+    # the usual 8 ms) is covered by the steps queued behind it. The sweeps of
+    # the contexts run one after the other (events order them): each pass of
+    # the balanced split is one wave of CTAs sized for the whole GPU, so two
+    # passes sharing the SMs would both run long.
+    e2e_value = e2e_serial = h2d_gbs = d2h_gbs = None
     if not args.skip_extras:
         host = [torch.empty((6, w.Ny, w.Nx), dtype=torch.float32, pin_memory=True) for _ in range(2)]
         sim.get_fields_host_f32(host[0].data_ptr())
@@ -293,31 +297,45 @@ def run_ours(args):
             sim.diagnostics()
             sim.get_fields_host_f32(host[0].data_ptr())
         e2e_serial = sites * S * e2e_steps * world / (time.perf_counter() - t0)
-        sim2 = Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
-                          chunk_rows=args.chunk_rows)
-        sims = (sim, sim2)
-        sim2.set_fields_host_f32(host[1].data_ptr())
-        sim2.step(S)
-        sim2.diagnostics()
-        torch.cuda.synchronize()
-        done = [torch.cuda.Event(), torch.cuda.Event()]
+        # the host copies alone (what the pipelined leg hides behind compute)
         t0 = time.perf_counter()
-        sims[0].set_fields_host_f32(host[0].data_ptr())
-        sims[0].step(S)
-        done[0].record(sims[0].stream)
-        for i in range(2 * e2e_steps):  # 2 x e2e_steps bench steps, two in flight
-            a, b = sims[i & 1], sims[(i + 1) & 1]
-            if i + 1 < 2 * e2e_steps:
-                b.set_fields_host_f32(host[(i + 1) & 1].data_ptr())
-                # the copy overlaps a's sweeps; b's sweeps follow them (each
-                # pass is one wave of CTAs sized for the whole GPU)
-                b.stream.wait_event(done[i & 1])
-                b.step(S)
-                done[(i + 1) & 1].record(b.stream)
-            a.diagnostics()
-            a.get_fields_host_f32(host[i & 1].data_ptr())
-        e2e_value = sites * S * 2 * e2e_steps * world / (time.perf_counter() - t0)
-        sim2.close()
+        for _ in range(3):
+            sim.set_fields_host_f32(host[0].data_ptr())
+            sim.synchronize()
+        h2d_gbs = 3 * 24 * sites / (time.perf_counter() - t0) / 1e9
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sim.get_fields_host_f32(host[0].data_ptr())
+        d2h_gbs = 3 * 24 * sites / (time.perf_counter() - t0) / 1e9
+        sims = [sim] + [Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
+                                   chunk_rows=args.chunk_rows) for _ in range(E2E_CONTEXTS - 1)]
+        P = len(sims)
+        host += [torch.empty_like(host[0], pin_memory=True) for _ in range(P - len(host))]
+        for k in range(1, P):
+            host[k].copy_(host[0])
+            sims[k].set_fields_host_f32(host[k].data_ptr())
+            sims[k].step(S)
+            sims[k].diagnostics()
+        torch.cuda.synchronize()
+        done = [torch.cuda.Event() for _ in range(P)]
+        nsteps = P * e2e_steps
+        t0 = time.perf_counter()
+        for i in range(nsteps + P - 1):
+            if i < nsteps:  # queue bench step i: upload, then sweep after step i - 1's sweeps
+                c = sims[i % P]
+                c.set_fields_host_f32(host[i % P].data_ptr())
+                if i > 0:
+                    c.stream.wait_event(done[(i - 1) % P])
+                c.step(S)
+                done[i % P].record(c.stream)
+            j = i - (P - 1)  # read back the oldest step in flight
+            if j >= 0:
+                d = sims[j % P]
+                d.diagnostics()
+                d.get_fields_host_f32(host[j % P].data_ptr())
+        e2e_value = sites * S * nsteps * world / (time.perf_counter() - t0)
+        for c in sims[1:]:
+            c.close()
     sim.close()
     if rank != 0:
         if world > 1:
@@ -350,9 +368,11 @@ def run_ours(args):
         "cpu_baseline": cb,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * sites * 4,
                 "d2h_bytes_per_step": 6 * sites * 4 + 40, "serial_value": e2e_serial,
+                "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs,
                 "note": "public C ABI with pinned host buffers; every bench step uploads its state, runs "
-                        "100 QLA steps + diagnostics and downloads the state; two contexts in flight (one's "
-                        "copies overlap the other's compute); serial_value: one context, copies in line"},
+                        "100 QLA steps + diagnostics and downloads the state; three contexts in flight (the copies "
+                        "of one step overlap the compute of the others); serial_value: one context, copies in "
+                        "line; *_gbs_alone: the host copies timed alone"},
         "clocks": clocks.summary(),
         "gpu_launches": args.steps * (launches_per_step + 2),
         "energy_last": last["energy"] if last else None,

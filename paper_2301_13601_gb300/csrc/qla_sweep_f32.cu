@@ -27,13 +27,16 @@ int sweep_block_rows(int precision, int K) {
 }
 
 // Balanced-split weights, measured on GB300 (8192^2, 2 steps per pass, two
-// CTAs per SM; per-CTA start and end times by globaltimer): the seam strip's
-// shares ran 1.10x (TM) and 1.19x (TE) as long per row as the others; the
-// first 152 TM CTAs (one per SM) 731.7 us against 806.9 us for the second
-// 152; the TE CTAs started over 256 us as the TM CTAs finished.
+// CTAs per SM; per-CTA start and end times by globaltimer, equal shares): the
+// seam strip's shares ran 1.10x (TM) and 1.19x (TE) as long per row as the
+// others; the first 152 TM CTAs (one per SM) 731.7 us against 806.9 us for
+// the second 152; the TE CTAs started over 256 us as the TM CTAs finished.
+// Throughput against the weights (G site-updates/s): equal shares 80.5; seam
+// rows 18, 19: 81.2; + older 3: 81.3; + start-order slope 6: 83.7, 8: 83.1,
+// 11: 82.3, 16: 80.9; older 5 with slope 8: 82.7.
 constexpr int kSeamRowCost[2] = {18, 19};  // sixteenths, TM, TE
 constexpr int kOlderShare64 = 3;           // profile 1
-constexpr int kStartOrderSlope64 = 8;      // profile 2
+constexpr int kStartOrderSlope64 = 6;      // profile 2
 
 SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma, int fam, int layer, int layers) {
     SweepSplit s;

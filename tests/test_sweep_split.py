@@ -13,7 +13,7 @@ the units exactly, and the bounds against a Python restatement of the
 documented cost model: 16 per row (the seam strip's rows 18 for TM, 19 for
 TE), 16 x (8K + R (K - 1)) warm-up at each strip start, shares weighted by
 profile (one layer or the first of two: the first half 1 + 3/64, the second
-1 - 3/64; the second of two layers: linearly from 1 + 8/64 down to 1 - 8/64),
+1 - 3/64; the second of two layers: linearly from 1 + 6/64 down to 1 - 6/64),
 the constants the library measured.
 """
 import numpy as np
@@ -24,7 +24,7 @@ from paper_2301_13601_gb300 import qla
 
 W_IN = 256
 SEAM_COST = {"TM": 18, "TE": 19}
-OLDER64, SLOPE64 = 3, 8
+OLDER64, SLOPE64 = 3, 6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -95,8 +95,8 @@ def test_share_profiles_at_8192():
     te = np.diff(qla.sweep_split(N, N, 2, 304, "fp32", "TE", 2)).astype(float)
     # first layer: the first 152 shares (past the seam strip's) 67/61 of the last 152
     assert abs(np.median(tm[20:152]) / np.median(tm[152:]) - 67 / 61) < 0.01
-    # second layer: rows fall linearly with the start order (weights 1 + a (1 - 2b / 303), a = 1/8)
-    w = lambda b: 1 + (1 - 2 * b / 303) / 8
+    # second layer: rows fall linearly with the start order (weights 1 + a (1 - 2b / 303), a = 6/64)
+    w = lambda b: 1 + (1 - 2 * b / 303) * 6 / 64
     assert abs(np.median(te[20:30]) / np.median(te[290:300]) - w(25) / w(295)) < 0.02
     # the seam strip's shares (strip 0, the first shares) hold 16/18 (TM) of the rows per cost
     assert abs(np.median(tm[1:8]) / np.median(tm[20:30]) - 16 / 18) < 0.02
