@@ -71,8 +71,8 @@ typedef struct {
     int precision;       /* QLA_FP32 (default) or QLA_FP64 (correctness mode) */
     int sequence;        /* QLA_SEQ_INTERLEAVED (default, Eq. 28) or QLA_SEQ_PLAIN (Eq. 23) */
     int potential;       /* QLA_POT_PAPER (default) or QLA_POT_UNITARY */
-    int steps_per_pass;  /* full time steps fused per HBM pass: 0 = automatic (FP64: 2; FP32: 2 from
-                            2^20 sites up (2^25 with chunk_rows set), else 4), else 1, 2 or 4 */
+    int steps_per_pass;  /* full time steps fused per HBM pass: 0 = automatic (2; FP32 with chunk_rows
+                            set: 2 from 2^25 sites up, else 4), else 1, 2 or 4 */
     int chunk_rows;      /* rows of one sweep tile, else 0 = automatic: each family's rows are
                             split into one share of equal estimated cost per resident CTA
                             (see qla_sweep_split) */

@@ -100,16 +100,16 @@ int sm_count(int dev) {
 }
 
 // Default steps per pass. FP32 with the balanced split: K = 2 (two CTAs per
-// SM, 112 KB of shared memory each) on lattices of at least 2^20 sites, else
-// K = 4 (one 224 KB CTA per SM). Measured on GB300 (three-cylinder workload,
-// site-updates/s, K = 2 vs K = 4): 6144^2 79.6 G vs 62.6 G; 4096^2 72.8 G vs
-// 51.5 G; 3072^2 66.7 G vs 48.5 G; 2048^2 50.8 G vs 37.3 G; 1024^2 24.6 G vs
-// 21.6 G. With fixed tiles (chunk_rows > 0) the second resident CTA paid only
-// from 2^25 sites up (tiles of 192 and 1024 rows: 8192^2 64.3 G vs 55.1 G,
-// 4096^2 42.6-44.4 G vs 43.4-44.0 G, 1024^2 19.9 G vs 25.4 G).
+// SM, 112 KB of shared memory each). Measured on GB300 (three-cylinder
+// workload, site-updates/s, K = 2 vs K = 4): 6144^2 79.6 G vs 62.6 G; 4096^2
+// 72.8 G vs 51.5 G; 3072^2 66.7 G vs 48.5 G; 2048^2 50.8 G vs 37.3 G; 1024^2
+// 24.6 G vs 21.6 G; 768^2 17.5 G vs 13.6 G; 512^2 8.5 G vs 7.2 G; 256^2 2.4 G
+// vs 2.1 G. With fixed tiles (chunk_rows > 0) the second resident CTA paid
+// only from 2^25 sites up (tiles of 192 and 1024 rows: 8192^2 64.3 G vs
+// 55.1 G, 4096^2 42.6-44.4 G vs 43.4-44.0 G, 1024^2 19.9 G vs 25.4 G).
 int default_steps_per_pass(int precision, int Nx, int Ny, int chunk_rows) {
     if (precision == QLA_FP64) return 2;
-    return (long long)Nx * Ny >= (chunk_rows > 0 ? (1LL << 25) : (1LL << 20)) ? 2 : 4;
+    return chunk_rows == 0 || (long long)Nx * Ny >= (1LL << 25) ? 2 : 4;
 }
 
 // CTAs per family of the balanced split of a pass of K steps: one per
