@@ -28,6 +28,7 @@ struct BatchInst {
     const void *coef;
     int Nx, Ny, w_valid, chunk, nsx, ncy, tiles, passes, vec;
     int tma, merged;  // tensor maps encoded (see BatchMaps); merged-level coefficient map encoded
+    int seam;         // the seam strip layout (SweepArgs::seam)
 };
 
 // TMA tensor maps of one instance (as SweepParams, for both state buffers),
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
         a.w_valid = I.w_valid;
         a.chunk = I.chunk;
         a.ctas = 0;
-        a.seam = 0;  // strips in the plain layout (the two at the x-edges copy with cp.async)
+        a.seam = I.seam;
         a.interleaved = INTER ? 1 : 0;
         a.unitary = UNIT ? 1 : 0;
         a.vec = I.vec;
@@ -344,9 +345,7 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
         I.Ny = d.Ny;
         I.w_valid = W - 8 * K;
         I.chunk = d.chunk_rows > 0 ? std::min(d.chunk_rows, d.Ny) : auto_batch_chunk(d.Ny);
-        I.nsx = (d.Nx + I.w_valid - 1) / I.w_valid;
         I.ncy = (d.Ny + I.chunk - 1) / I.chunk;
-        I.tiles = I.nsx * I.ncy;
         I.passes = int(d.nsteps / K);
         I.vec = 1;
         float *q0, *q1, *coef;
@@ -381,11 +380,14 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
         cudaFree(idx);
         b->allocs.pop_back();
     }
-    // TMA tensor maps of every instance (both state buffers); an instance whose
-    // maps cannot be encoded copies with cp.async
+    // TMA tensor maps of every instance (both state buffers) and its strips:
+    // the seam layout where TMA applies (every strip copies with TMA); an
+    // instance whose maps cannot be encoded copies with cp.async in the plain
+    // layout
     std::vector<qla::BatchMaps> maps(count);
     for (int k = 0; k < count; ++k) {
         qla::BatchInst &I = b->inst[k];
+        I.seam = qla::make_sweep_split(I.Nx, I.Ny, K, qla::kBatchRows, 1).seam;
         bool ok = true;
         for (int par = 0; par < 2 && ok; ++par) {
             qla::SweepArgs a;
@@ -396,12 +398,17 @@ qla_status qla_batch_create(int count, const qla_instance_desc *descs, const qla
             a.Ny = I.Ny;
             a.w_valid = I.w_valid;
             a.chunk = I.chunk;
+            a.seam = I.seam;
             int merged = 0;
             memset(&maps[k].m[par], 0, sizeof(qla::SweepMaps));
             ok = qla::make_sweep_maps(a, K, qla::kBatchRows, maps[k].m[par], &merged);
             if (par == 0) I.merged = merged;
         }
         I.tma = ok ? 1 : 0;
+        const qla::SweepSplit sp = qla::make_sweep_split(I.Nx, I.Ny, K, qla::kBatchRows, I.tma);
+        I.seam = sp.seam;
+        I.nsx = sp.nsx;
+        I.tiles = I.nsx * I.ncy;
     }
     // schedule tables
     b->maxpass = b->inst[0].passes;

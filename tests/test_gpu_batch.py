@@ -18,9 +18,11 @@ from paper_2301_13601_gb300.qla import Batch, Simulation
 pytestmark = pytest.mark.gpu
 
 # (Nx, Ny, nsteps, polarisation, chunk_rows): uneven sizes, several strips and
-# chunks, steps multiples of 4, a lattice narrower than a strip
+# chunks, steps multiples of 4, a lattice narrower than a strip; Nx a multiple
+# of 8 from 256 up (256, 512, 776) sweeps in the seam layout (strip 0 across
+# x = 0, every strip on TMA), the others in the plain layout
 CASES = [(64, 48, 8, "Ez", 0), (128, 100, 12, "Ey", 24), (200, 64, 16, "Ez", 0), (256, 256, 4, "Ey", 96),
-         (300, 70, 20, "Ez", 16), (96, 96, 24, "Ey", 0)]
+         (300, 70, 20, "Ez", 16), (96, 96, 24, "Ey", 0), (512, 64, 8, "Ez", 0), (776, 40, 12, "Ey", 16)]
 
 
 def make_instances(K=4):
