@@ -31,8 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes per sweep launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture
-# (one pass) of two sweep launches of this benchmark's own command on the 8192^2 workload
-# (profiles/sweep_kernel_cylinders8192_launches.md), valid while the sweep's code (comment lines
+# (one pass) of two sweep launches of this benchmark's own command on the 8192^2 workload (its
+# summary sits in profiles/ beside the launch list), valid while the sweep's code (comment lines
 # excluded), the workload, the steps per pass and the launch form (balanced split) match.
 MEASURED_TRAFFIC = {"sweep_sha256_prefix": "431381dc86281234", "workload": "cylinders8192_fp32",
                     "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 7.77460e9}
