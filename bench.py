@@ -33,9 +33,10 @@ sys.path.insert(0, ROOT)
 # DRAM bytes per sweep launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture
 # (one pass) of two sweep launches of this benchmark's own command on the 8192^2 workload (its
 # summary sits in profiles/ beside the launch list), valid while the sweep's code (comment lines
-# excluded), the workload, the steps per pass and the launch form (balanced split) match.
+# excluded), the workload, the steps per pass and the launch form (balanced split, one launch per
+# pass or all passes of a bench step in one persistent launch) match.
 MEASURED_TRAFFIC = {"sweep_sha256_prefix": "431381dc86281234", "workload": "cylinders8192_fp32",
-                    "steps_per_pass": 2, "chunk_rows": 0, "bytes_per_launch": 7.77460e9}
+                    "steps_per_pass": 2, "chunk_rows": 0, "launch": "per_pass", "bytes_per_launch": 7.77460e9}
 
 L2_BYTES = 129e6  # GB300 L2
 METRIC = "site-updates/s per QLA step"
@@ -120,7 +121,7 @@ def sweep_code_hash() -> str:
     import hashlib
 
     code = []
-    for name in ("qla_sweep.cuh", "qla_sweep_f32.cu", "qla_internal.h"):
+    for name in ("qla_sweep.cuh", "qla_sweep_f32.cu", "qla_sweep_persist.cu", "qla_internal.h"):
         with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", name)) as f:
             code += [l for l in f.read().splitlines() if not l.lstrip().startswith("//")]
     return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
@@ -232,7 +233,7 @@ def run_ours(args):
     n = w.medium()
     S = QLA_STEPS_PER_BENCH_STEP
     sim = Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
-                     chunk_rows=args.chunk_rows)
+                     chunk_rows=args.chunk_rows, launch=args.launch)
     sim.init_pulse("Ez" if w.pulse.pol == media.POL_EZ else "Ey", w.pulse.x0, w.pulse.sigma, w.pulse.amp)
     stream = sim.stream
     sites = w.Nx * w.Ny
@@ -269,7 +270,9 @@ def run_ours(args):
     value, total_ms = job_throughput(sites * S * args.steps, total_ms, world, device="cuda")
     if world > 1:
         dist.barrier()
-    launches_per_step = math.ceil(S / sim.steps_per_pass)
+    # one launch per pass, or every pass of a bench step in one persistent launch
+    launch_form = sim.launch
+    launches_per_step = 1 if launch_form == "persistent" else math.ceil(S / sim.steps_per_pass)
     # e2e through the public API with host buffers: pinned H2D state copy,
     # qla_step, diagnostics, D2H state copy, every bench step. Serial: one
     # context, each step's copies between its compute. Pipelined (the reported
@@ -308,7 +311,7 @@ def run_ours(args):
             sim.get_fields_host_f32(host[0].data_ptr())
         d2h_gbs = 3 * 24 * sites / (time.perf_counter() - t0) / 1e9
         sims = [sim] + [Simulation(*n, w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
-                                   chunk_rows=args.chunk_rows) for _ in range(E2E_CONTEXTS - 1)]
+                                   chunk_rows=args.chunk_rows, launch=args.launch) for _ in range(E2E_CONTEXTS - 1)]
         P = len(sims)
         host += [torch.empty_like(host[0], pin_memory=True) for _ in range(P - len(host))]
         for k in range(1, P):
@@ -346,10 +349,12 @@ def run_ours(args):
     sha = sweep_code_hash()
     traffic = None
     if (sha == MEASURED_TRAFFIC["sweep_sha256_prefix"] and w.name == MEASURED_TRAFFIC["workload"]
-            and k == MEASURED_TRAFFIC["steps_per_pass"] and sim.chunk_rows == MEASURED_TRAFFIC["chunk_rows"]):
+            and k == MEASURED_TRAFFIC["steps_per_pass"] and sim.chunk_rows == MEASURED_TRAFFIC["chunk_rows"]
+            and launch_form == MEASURED_TRAFFIC["launch"]):
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     launch_ms = sweep_ms / (args.steps * launches_per_step)
-    achieved = BYTES_PER_SITE_UPDATE * sites * k / (launch_ms / 1e3) / 1e9
+    steps_per_launch = S / launches_per_step
+    achieved = BYTES_PER_SITE_UPDATE * sites * steps_per_launch / (launch_ms / 1e3) / 1e9
     cb = None if args.skip_extras else cpu_baseline(seconds=args.cpu_seconds)[0]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -357,14 +362,17 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "lattice": f"{w.Nx}x{w.Ny}", "delta": w.delta,
                    "qla_steps_per_bench_step": S, "steps_per_pass": k, "chunk_rows": sim.chunk_rows,
+                   "launch": launch_form,
                    "precision": "fp32", "sequence": "interleaved", "potential": "paper",
                    "l2": (f"inputs {'larger' if 80 * sites > L2_BYTES else 'smaller'} than L2 (state "
                           f"{24 * sites / 1e9:.2f} GB + coefficients {56 * sites / 1e9:.2f} GB read per pass)"),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"sweep_kernel<float,{k}>", "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
-                     "note": "algorithmic bytes of the unfused step x steps fused per launch"},
+                     "kernel": (f"sweep_persistent_kernel<float,{k}> ({S // k} passes per launch)"
+                                if launch_form == "persistent" else f"sweep_kernel<float,{k}>"),
+                     "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
+                     "note": "algorithmic bytes of the unfused step x steps per launch"},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * sites * 4,
                 "d2h_bytes_per_step": 6 * sites * 4 + 40, "serial_value": e2e_serial,
@@ -403,7 +411,8 @@ def single_family_report(w, args, peak, peak_kind, steps: int = 5):
     alg = 28.0 if fam == "TM" else 32.0
     S = QLA_STEPS_PER_BENCH_STEP
     with Simulation(*w.medium(), w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
-                    chunk_rows=args.chunk_rows, families=fam) as sim:
+                    chunk_rows=args.chunk_rows, families=fam, launch=args.launch) as sim:
+        form = sim.launch
         sim.init_pulse(pol, w.pulse.x0, w.pulse.sigma, w.pulse.amp)
         sim.step(S)
         sim.diagnostics()
@@ -417,7 +426,7 @@ def single_family_report(w, args, peak, peak_kind, steps: int = 5):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
     value = w.Nx * w.Ny * S / (ms / 1e3)
-    return {"families": fam, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+    return {"families": fam, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "launch": form,
             "bytes_per_site_update": alg, "bandwidth_equivalent_frac": value * alg / 1e9 / peak,
             "peak_kind": peak_kind, "note": "same bench step (100 QLA steps + diagnostics); the other family's "
             "planes are zero and stay zero (Eq. 17-22 never couple the families)"}
@@ -683,6 +692,8 @@ def main():
                     default="cylinders8192")
     ap.add_argument("--batch-step-scale", type=int, default=10, help="batch64: steps of each lattice divided by this")
     ap.add_argument("--chunk-rows", type=int, default=0)
+    ap.add_argument("--launch", choices=["auto", "per_pass", "persistent"], default="auto",
+                    help="sweep launch form: one launch per pass, or every pass of a bench step in one launch")
     ap.add_argument("--skip-extras", action="store_true", help="no e2e leg and no CPU baseline (profiling runs)")
     ap.add_argument("--skip-surrogate", action="store_true", help="no surrogate evaluation")
     args = ap.parse_args()

@@ -60,6 +60,18 @@ enum { QLA_POL_EZ = 0, QLA_POL_EY = 1 };                    /* pulse polarisatio
  * with only one family's components nonzero keeps the other family at exactly
  * zero, so advancing one family gives the same result at half the work. */
 enum { QLA_FAMILIES_BOTH = 0, QLA_FAMILY_TM = 1, QLA_FAMILY_TE = 2 };
+/* How qla_step launches the passes of the balanced split (qla_options.launch).
+ * QLA_LAUNCH_PER_PASS: one kernel launch per pass of steps_per_pass steps.
+ * QLA_LAUNCH_PERSISTENT: all the full passes of one qla_step call in one
+ *   cooperative launch, one CTA per resident slot; CTA b sweeps share b of each
+ *   advanced family in every pass and, before a pass, waits only for the shares
+ *   whose previous pass wrote what it reads or read what it overwrites (see
+ *   qla_sweep_dependencies), not for the whole lattice. Bit-identical results.
+ *   Applies to FP32 contexts with the balanced split (chunk_rows = 0), 2 steps
+ *   per pass, Nx a multiple of 8 and at least 256; other contexts, and a launch
+ *   the device refuses, use one launch per pass.
+ * QLA_LAUNCH_AUTO: one launch per pass (the faster form where measured). */
+enum { QLA_LAUNCH_AUTO = 0, QLA_LAUNCH_PER_PASS = 1, QLA_LAUNCH_PERSISTENT = 2 };
 
 /* Options for qla_create. Obtain defaults with qla_default_options().
  * potential: QLA_POT_PAPER applies V_X, V_Y as printed (Eq. 21-22, with
@@ -82,6 +94,7 @@ typedef struct {
                             family is stored and advanced; the other family's components are
                             held at zero (qla_set_fields* ignore them, qla_get_fields* return
                             zeros, qla_init_pulse requires the matching polarisation) */
+    int launch;          /* QLA_LAUNCH_AUTO (default), QLA_LAUNCH_PER_PASS or QLA_LAUNCH_PERSISTENT */
 } qla_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -254,6 +267,12 @@ long long qla_step_count(const qla_ctx *ctx);
  * (0: the balanced split), and the precision. Any pointer may be NULL. */
 qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_rows, int *precision);
 
+/* The launch form qla_step uses for the context's passes of steps_per_pass
+ * steps: QLA_LAUNCH_PERSISTENT or QLA_LAUNCH_PER_PASS (the option resolved
+ * against what the context allows; PER_PASS after the device refused a
+ * cooperative launch). QLA_EINVAL on NULL. */
+qla_status qla_get_launch(const qla_ctx *ctx, int *launch);
+
 /* The balanced split of one fused pass of steps_per_pass steps (the sweep of
  * Eq. 28 / Eq. 23 over the lattice, one CTA grid layer per family). The
  * lattice is cut into strips of 256 - 8K output columns (K = steps_per_pass;
@@ -277,7 +296,27 @@ qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_ro
 qla_status qla_sweep_split(int Nx, int Ny, int precision, int steps_per_pass, int ctas, int family, int layers,
                            long long *bounds, int capacity);
 
-/* The split the context's passes of steps_per_pass steps use for `family`:
+/* The shares that share `share` of the persistent launch form waits for
+ * before each of its passes after the first (QLA_LAUNCH_PERSISTENT): the other
+ * shares of the same family (split as qla_sweep_split with layers = 1, FP32)
+ * whose previous pass wrote a cell that it reads or read a cell that it
+ * overwrites. A segment of rows [y0, y1) of a strip writes those rows of the
+ * strip's output columns and reads rows [y0 - 4K, y1 + 4K + R - 1) of its 256
+ * input columns (a pass of K steps has dependency radius 4K along each axis,
+ * Eq. 18 and Eq. 20; R = 4 rows per iteration); the test takes rows
+ * [y0 - 4K - R, y1 + 4K + R) against the other share's rows, either way, so
+ * the list may hold a few more shares than strictly needed, never fewer.
+ * Writes the share indices in increasing order to deps (caller-owned,
+ * capacity entries) and their number to *count. Host arithmetic only (the
+ * same function the kernel evaluates): needs no GPU. QLA_EINVAL on a bad
+ * size, family, CTA count, share or capacity; QLA_EUNSUPPORTED if the
+ * persistent form is not built for steps_per_pass or the lattice has no seam
+ * layout (Nx not a multiple of 8, or below 256). */
+qla_status qla_sweep_dependencies(int Nx, int Ny, int steps_per_pass, int ctas, int family, int share, int *deps,
+                                  int capacity, int *count);
+
+/* The split the context's passes of steps_per_pass steps use for `family`
+ * (with the persistent launch form, one layer's split per family):
  * *ctas = CTAs of the family's layer (0 when the context sweeps tiles of
  * chunk_rows rows instead, or does not advance the family), and, if bounds is
  * not NULL and *ctas > 0, the share bounds as qla_sweep_split writes them

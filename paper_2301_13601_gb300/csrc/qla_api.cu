@@ -34,6 +34,9 @@ struct qla_ctx {
     int K = 4;
     int chunk = 0;
     int ctas[5] = {0, 0, 0, 0, 0};  // balanced split (chunk == 0): CTAs per family of a pass of K steps
+    bool persistent = false;        // passes of K steps in one cooperative launch per qla_step (QLA_LAUNCH_*)
+    unsigned *pass_done = nullptr;  // device [2][kPersistMaxCtas]: passes completed per share (persistent form)
+    unsigned pass_epoch = 0;        // passes the persistent launches have completed (the counters' base)
     long long steps = 0;
     bool has_state = false;
     qla_status sticky = QLA_OK;
@@ -43,6 +46,7 @@ struct qla_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kPassCounterBytes = 2 * size_t(qla::kPersistMaxCtas) * sizeof(unsigned);
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -120,6 +124,15 @@ int balanced_ctas(int Nx, int Ny, int K, int prec, int interleaved, int sms) {
     return int(std::min((long long)sms * occ, (long long)sp.nsx * Ny));
 }
 
+// Whether the context's passes of K steps can take the persistent launch form:
+// FP32, the balanced split, K instantiated for it, the seam layout (Nx a
+// multiple of 8, at least 256 columns) and at most kPersistMaxCtas shares.
+bool persistent_applies(const qla_ctx *c) {
+    return c->opt.precision == QLA_FP32 && c->chunk == 0 && qla::sweep_persistent_supported(0, c->K) &&
+           c->Nx % 8 == 0 && c->Nx >= qla::sweep_strip_width() && c->ctas[c->K] >= 1 &&
+           c->ctas[c->K] <= qla::kPersistMaxCtas;
+}
+
 // Whether component `comp` (Eq. 15 order) belongs to a family the context
 // advances: TM = (q2, q3, q4), TE = (q0, q1, q5).
 bool family_has(const qla_ctx *c, int comp) {
@@ -151,6 +164,41 @@ qla_status launch_pass(qla_ctx *c, int K) {
                                                   : qla::launch_sweep_f32(K, a, nfam, c->stream);
     if (e != cudaSuccess) return fail(c, QLA_ECUDA, "sweep launch (K=%d): %s", K, cudaGetErrorString(e));
     c->cur ^= 1;
+    return QLA_OK;
+}
+
+// `passes` passes of K = c->K steps in one cooperative launch. *refused: the
+// device did not take the launch (nothing ran; the caller falls back to one
+// launch per pass).
+qla_status launch_persistent(qla_ctx *c, int passes, bool *refused) {
+    *refused = false;
+    const int K = c->K;
+    qla::SweepArgs a{};
+    a.q_in = c->state[c->cur];
+    a.q_out = c->state[c->cur ^ 1];
+    a.coef = c->coef;
+    a.Nx = c->Nx;
+    a.Ny = c->Ny;
+    a.w_valid = qla::sweep_strip_width() - 8 * K;
+    a.chunk = 0;
+    a.ctas = c->ctas[K];
+    a.order = nullptr;
+    a.interleaved = c->opt.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0;
+    a.unitary = c->opt.potential == QLA_POT_UNITARY ? 1 : 0;
+    a.vec = (c->Nx % int(16 / c->esize)) == 0 ? 1 : 0;
+    const int nfam = c->opt.families == QLA_FAMILIES_BOTH ? 2 : 1;
+    a.fam0 = c->opt.families == QLA_FAMILY_TE ? 1 : 0;
+    a.error = c->sweep_err;
+    const cudaError_t e =
+        qla::launch_sweep_persistent_f32(K, a, nfam, passes, c->pass_epoch, c->pass_done, c->stream);
+    if (e == cudaErrorNotSupported || e == cudaErrorCooperativeLaunchTooLarge) {
+        cudaGetLastError();
+        *refused = true;
+        return QLA_OK;
+    }
+    if (e != cudaSuccess) return fail(c, QLA_ECUDA, "persistent sweep launch (K=%d): %s", K, cudaGetErrorString(e));
+    c->pass_epoch += unsigned(passes);
+    if (passes & 1) c->cur ^= 1;
     return QLA_OK;
 }
 
@@ -188,6 +236,7 @@ void qla_default_options(qla_options *opt) {
     opt->device = -1;
     opt->stream = nullptr;
     opt->families = QLA_FAMILIES_BOTH;
+    opt->launch = QLA_LAUNCH_AUTO;
 }
 
 qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_buffer_sizes *out) {
@@ -201,7 +250,8 @@ qla_status qla_query_buffer_sizes(int Nx, int Ny, const qla_options *opt, qla_bu
     out->coeff_bytes = round_up(size_t(qla::NCOEF) * P * es, kAlign);
     out->index_bytes = round_up(3 * P * sizeof(double), kAlign);
     out->scratch_bytes = round_up(qla::diag_scratch_bytes(Nx, Ny), kAlign) + round_up(sizeof(qla::DiagResult), kAlign) +
-                         kAlign;  // sweep error flag, share-order counter
+                         kAlign +  // sweep error flag, share-order counter
+                         kPassCounterBytes;  // per-share pass counters of the persistent launch form
     return QLA_OK;
 }
 
@@ -219,6 +269,8 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
     if (o.families != QLA_FAMILIES_BOTH && o.families != QLA_FAMILY_TM && o.families != QLA_FAMILY_TE)
         return QLA_EINVAL;
     if (o.steps_per_pass < 0 || o.chunk_rows < 0) return QLA_EINVAL;
+    if (o.launch != QLA_LAUNCH_AUTO && o.launch != QLA_LAUNCH_PER_PASS && o.launch != QLA_LAUNCH_PERSISTENT)
+        return QLA_EINVAL;
     if (o.steps_per_pass > 0 && !qla::sweep_supported(o.precision, o.steps_per_pass)) return QLA_EUNSUPPORTED;
     const size_t P = size_t(Nx) * size_t(Ny);
     const double *nn[3] = {n_x, n_y, n_z};
@@ -283,6 +335,8 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
     // the sweep error flag and, 64 bytes on in the same slot, the share-order counter
     c->share_order = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(c->sweep_err) + 64);
     if (cudaMemsetAsync(c->sweep_err, 0, kAlign, c->stream) != cudaSuccess) return bail(QLA_ECUDA);
+    c->pass_done = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(c->sweep_err) + kAlign);
+    if (cudaMemsetAsync(c->pass_done, 0, kPassCounterBytes, c->stream) != cudaSuccess) return bail(QLA_ECUDA);
     for (int k = 0; k < 3; ++k)
         if (cudaMemcpyAsync(c->index + size_t(k) * P, nn[k], P * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream) != cudaSuccess)
@@ -302,6 +356,10 @@ qla_status qla_create(int Nx, int Ny, const double *n_x, const double *n_y, cons
             if (qla::sweep_supported(o.precision, k))
                 c->ctas[k] = balanced_ctas(Nx, Ny, k, o.precision == QLA_FP64 ? 1 : 0,
                                            o.sequence == QLA_SEQ_INTERLEAVED ? 1 : 0, sm_count(c->dev));
+    // QLA_LAUNCH_AUTO: one launch per pass, measured the faster form (the persistent one on GB300, 8192^2,
+    // 2 steps per pass, site-updates/s: both families 62.1 G with the families alternating per pass against
+    // 83.5 G; TM alone 161.2 against 164.6 G; TE alone 166.2 against 163.5 G)
+    c->persistent = o.launch == QLA_LAUNCH_PERSISTENT && persistent_applies(c);
     c->has_state = true;  // zero state
     *out = c;
     return QLA_OK;
@@ -384,6 +442,19 @@ qla_status qla_step(qla_ctx *c, long long nsteps) {
     if (nsteps < 0) return fail(c, QLA_EINVAL, "qla_step: nsteps < 0");
     if (!c->has_state) return fail(c, QLA_ESTATE, "qla_step: no state");
     long long left = nsteps;
+    // the full passes in cooperative launches (at most 2^20 passes each)
+    while (c->persistent && left >= c->K) {
+        const int passes = int(std::min(left / c->K, 1LL << 20));
+        bool refused = false;
+        s = launch_persistent(c, passes, &refused);
+        if (s != QLA_OK) return s;
+        if (refused) {  // from now on one launch per pass
+            c->persistent = false;
+            break;
+        }
+        left -= (long long)passes * c->K;
+        c->steps += (long long)passes * c->K;
+    }
     while (left > 0) {
         int k = c->K;
         while (k > 1 && (k > left || !qla::sweep_supported(c->opt.precision, k))) --k;
@@ -543,8 +614,39 @@ qla_status qla_get_sweep_split(const qla_ctx *c, int steps_per_pass, int family,
     const bool advanced = c->opt.families == QLA_FAMILIES_BOTH || c->opt.families == family;
     *ctas = c->chunk > 0 || !advanced ? 0 : c->ctas[steps_per_pass];
     if (*ctas == 0 || !bounds) return QLA_OK;
-    return qla_sweep_split(c->Nx, c->Ny, c->opt.precision, steps_per_pass, *ctas, family,
-                           c->opt.families == QLA_FAMILIES_BOTH ? 2 : 1, bounds, capacity);
+    // the persistent form sweeps one layer's split per family
+    const bool one_layer = c->opt.families != QLA_FAMILIES_BOTH || (c->persistent && steps_per_pass == c->K);
+    return qla_sweep_split(c->Nx, c->Ny, c->opt.precision, steps_per_pass, *ctas, family, one_layer ? 1 : 2, bounds,
+                           capacity);
+}
+
+qla_status qla_sweep_dependencies(int Nx, int Ny, int steps_per_pass, int ctas, int family, int share, int *deps,
+                                  int capacity, int *count) {
+    if (Nx < 1 || Ny < 1 || !deps || !count || capacity < 0) return QLA_EINVAL;
+    if (family != QLA_FAMILY_TM && family != QLA_FAMILY_TE) return QLA_EINVAL;
+    if (ctas < 1 || ctas > qla::kPersistMaxCtas || share < 0 || share >= ctas) return QLA_EINVAL;
+    if (!qla::sweep_persistent_supported(0, steps_per_pass)) return QLA_EUNSUPPORTED;
+    const qla::SweepSplit sp = qla::make_sweep_split(Nx, Ny, steps_per_pass, qla::sweep_block_rows(0, steps_per_pass),
+                                                     1, family == QLA_FAMILY_TE ? 1 : 0, 0, 1);
+    if (!sp.seam) return QLA_EUNSUPPORTED;
+    if ((long long)sp.nsx * Ny >= (1LL << 31)) return QLA_EINVAL;
+    const long long b0 = sp.share_begin(share, ctas), b1 = sp.share_begin(share + 1, ctas);
+    int n = 0;
+    for (int d = 0; d < ctas; ++d) {
+        if (d == share ||
+            !sp.shares_touch(b0, b1, sp.share_begin(d, ctas), sp.share_begin(d + 1, ctas), qla::sweep_strip_width()))
+            continue;
+        if (n >= capacity) return QLA_EINVAL;
+        deps[n++] = d;
+    }
+    *count = n;
+    return QLA_OK;
+}
+
+qla_status qla_get_launch(const qla_ctx *c, int *launch) {
+    if (!c || !launch) return QLA_EINVAL;
+    *launch = c->persistent ? QLA_LAUNCH_PERSISTENT : QLA_LAUNCH_PER_PASS;
+    return QLA_OK;
 }
 
 const char *qla_last_error(const qla_ctx *c) { return c ? c->msg.c_str() : "NULL context"; }

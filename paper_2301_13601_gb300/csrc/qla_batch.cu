@@ -53,18 +53,6 @@ struct BatchSched {
     unsigned int withhold;           // test hook: extra completions a dependency waits for (0 normally)
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB)
     batch_kernel(const BatchSched S) {

@@ -71,6 +71,7 @@ struct SweepSplit {
     int w_seam;   // cost of a row of the seam strip (sixteenths)
     int profile;  // share sizes (above)
     int p64;
+    int K, R;     // steps per pass, rows per iteration
 
     __host__ __device__ long long strip0_cost() const {
         return 16LL * warm + (long long)(seam ? w_seam : 16) * Ny;
@@ -107,6 +108,71 @@ struct SweepSplit {
             den = 64LL * G * (G - 1);
         }
         return unit_of_cost(cost_total() / den * num + cost_total() % den * num / den);
+    }
+
+    // Columns of strip s, as circular intervals mod Nx: it reads w_in columns
+    // from *rd (its halo of 4K columns either side included) and writes *ow
+    // columns from *o0 (the sweep kernel's strip geometry, SweepArgs::seam).
+    __host__ __device__ void strip_cols(int s, int w_in, int *rd, int *o0, int *ow) const {
+        const int h = 4 * K;
+        int r, o, w;
+        if (!seam) {
+            o = s * w_valid;
+            w = Nx - o < w_valid ? Nx - o : w_valid;
+            r = o - h;
+        } else if (s == 0) {
+            r = Nx - w_in / 2;
+            o = r + h;
+            w = w_in - 2 * h;
+        } else {
+            o = w_in / 2 - h + (s - 1) * w_valid;
+            const int hi = Nx - w_in / 2 + h;
+            w = (o + w_valid < hi ? o + w_valid : hi) - o;
+            r = o - h < Nx - w_in ? o - h : Nx - w_in;
+        }
+        *rd = ((r % Nx) + Nx) % Nx;
+        *o0 = ((o % Nx) + Nx) % Nx;
+        *ow = w;
+    }
+    // Whether [a, a + la) and [b, b + lb) meet on a circle of n points
+    // (0 <= a, b < n; la, lb >= 1; a length >= n is the whole circle).
+    __host__ __device__ static bool circ_meet(int a, int la, int b, int lb, int n) {
+        if (la >= n || lb >= n) return true;
+        const int ba = b >= a ? b - a : b - a + n;
+        const int ab = a >= b ? a - b : a - b + n;
+        return ba < la || ab < lb;
+    }
+    // Whether the shares of units [b0, b1) and [d0, d1) of consecutive passes
+    // must be ordered: one writes a cell that the other reads (on the same
+    // state buffer, the later pass's read after the earlier pass's write, or
+    // its write after the earlier pass's read). A segment writes rows
+    // [y0, y1) of its strip's output columns and reads rows [y0 - 4K,
+    // y1 + 4K + R - 1) of its input columns (level 0 is fed from y0 - 4K and
+    // its last R-row block starts at y1 + 4K - 1 at the latest); both
+    // directions are covered by rows [y0 - 4K - R, y1 + 4K + R) against the
+    // other's rows, and input columns against output columns either way.
+    __host__ __device__ bool shares_touch(long long b0, long long b1, long long d0, long long d1, int w_in) const {
+        for (long long u = b0; u < b1;) {
+            const int s = int(u / Ny);
+            const int y0 = int(u - (long long)s * Ny);
+            const int y1 = (long long)(Ny - y0) < b1 - u ? Ny : y0 + int(b1 - u);
+            u += y1 - y0;
+            int rs, os, ws;
+            strip_cols(s, w_in, &rs, &os, &ws);
+            const int wl = y1 - y0 + 8 * K + 2 * R;
+            const int ws0 = (((y0 - 4 * K - R) % Ny) + Ny) % Ny;
+            for (long long v = d0; v < d1;) {
+                const int t = int(v / Ny);
+                const int z0 = int(v - (long long)t * Ny);
+                const int z1 = (long long)(Ny - z0) < d1 - v ? Ny : z0 + int(d1 - v);
+                v += z1 - z0;
+                if (!circ_meet(ws0, wl, z0, z1 - z0, Ny)) continue;
+                int rt, ot, wt;
+                strip_cols(t, w_in, &rt, &ot, &wt);
+                if (circ_meet(rs, w_in, ot, wt, Nx) || circ_meet(rt, w_in, os, ws, Nx)) return true;
+            }
+        }
+        return false;
     }
 };
 
@@ -150,6 +216,16 @@ struct SweepArgs {
 cudaError_t launch_sweep_f32(int K, const SweepArgs &a, int nfam, cudaStream_t st);
 cudaError_t launch_sweep_f64(int K, const SweepArgs &a, int nfam, cudaStream_t st);
 bool sweep_supported(int precision, int K);
+// Persistent form of the balanced split (qla_sweep_persist.cu): `passes`
+// passes of K steps in one cooperative launch of a.ctas CTAs (at most
+// kPersistMaxCtas), CTA b sweeping share b of each of the nfam families in
+// turn, ordered by the per-share pass counters done[nfam][a.ctas] (their
+// values before the launch all <= base). FP32 with tensor maps and the seam
+// layout only: cudaErrorNotSupported otherwise.
+constexpr int kPersistMaxCtas = 4096;
+cudaError_t launch_sweep_persistent_f32(int K, const SweepArgs &a, int nfam, int passes, unsigned base,
+                                        unsigned *done, cudaStream_t st);
+bool sweep_persistent_supported(int precision, int K);
 int sweep_strip_width();  // input columns per strip (halo included)
 int sweep_occupancy_f32(int K, int interleaved);  // resident CTAs per SM
 int sweep_occupancy_f64(int K, int interleaved);

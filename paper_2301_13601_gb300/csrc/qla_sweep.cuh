@@ -54,6 +54,24 @@ namespace qla {
 constexpr int LANE_COLS = 8;
 constexpr int W_IN = 32 * LANE_COLS;
 
+// Global nanosecond timer (bounds the waits on other CTAs' progress).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Progress counters written by other CTAs: acquire loads and release stores
+// at GPU scope.
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Tensor maps for the TMA loads of one FP32 pass: the input state viewed as
 // [6][Ny][Nx/8][8] floats with the 32-byte swizzle and the coefficient pairs
 // as [7][Ny][Nx/8][16] floats with the 64-byte swizzle. One box row (8 x 32,
@@ -426,9 +444,13 @@ struct YPipe {
 // Returns true (uniformly over the CTA) if the error flag is set (a bounded
 // copy wait ran out); the CTA's copy barriers are then left as they are and
 // the caller stops.
-template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM>
+// TMA_ONLY: the caller guarantees TMA copies for every strip (the seam
+// layout); the per-lane copy path is compiled out, and a strip that could not
+// copy with TMA sets the error flag instead.
+template <typename T, int K, int R, int NY, bool INTER, bool UNIT, int FAM, bool TMA_ONLY = false>
 __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb, int ye, unsigned char *smem_raw,
-                                           const SweepMaps *M = nullptr, bool merged = false) {
+                                           const SweepMaps *M = nullptr, bool merged = false,
+                                           bool swap = false) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     using T2 = typename Ar<T>::T2;
@@ -449,8 +471,9 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
 
     const int Nx = A.Nx, Ny = A.Ny;
     const int P = Nx * Ny;  // < 2^31 (checked on the host)
-    const T *__restrict__ qin = static_cast<const T *>(A.q_in);
-    T *__restrict__ qout = static_cast<T *>(A.q_out);
+    // swap: read A.q_out and write A.q_in (the odd passes of a persistent launch)
+    const T *__restrict__ qin = static_cast<const T *>(swap ? A.q_out : A.q_in);
+    T *__restrict__ qout = static_cast<T *>(swap ? const_cast<void *>(A.q_in) : A.q_out);
     const T2 *__restrict__ cpairs = static_cast<const T2 *>(A.coef);
     const bool vec = A.vec != 0;
 
@@ -549,6 +572,13 @@ __device__ __forceinline__ bool sweep_body(const SweepArgs &A, int strip, int yb
     bool use_tma = false;
     if constexpr (std::is_same<T, float>::value)
         use_tma = M != nullptr && ((nowrap && (xb & 7) == 0) || seam_strip) && (tc::smem_addr(smem_raw) & 1023u) == 0;
+    if constexpr (TMA_ONLY) {
+        if (!use_tma) {  // uniform over the CTA
+            if (A.error) atomicExch(A.error, 1);
+            return true;
+        }
+        use_tma = true;
+    }
     uint32_t tph_x = 0, tph_y = 0;
     constexpr uint32_t SROW = W_IN * sizeof(T), CROW = W_IN * sizeof(T2);
     // the R rows of a block (level j) of one pair plane: one box, or R one-row

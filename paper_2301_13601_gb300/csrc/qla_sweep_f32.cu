@@ -50,6 +50,8 @@ SweepSplit make_sweep_split(int Nx, int Ny, int K, int R, int tma, int fam, int 
     s.w_seam = kSeamRowCost[fam ? 1 : 0];
     s.profile = layers == 2 && layer == 1 ? 2 : 1;
     s.p64 = s.profile == 2 ? kStartOrderSlope64 : kOlderShare64;
+    s.K = K;
+    s.R = R;
     return s;
 }
 

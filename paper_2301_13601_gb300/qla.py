@@ -22,6 +22,8 @@ SEQ_INTERLEAVED, SEQ_PLAIN = 0, 1
 POT_PAPER, POT_UNITARY = 0, 1
 POL_EZ, POL_EY = 0, 1
 FAMILIES_BOTH, FAMILY_TM, FAMILY_TE = 0, 1, 2
+LAUNCH_AUTO, LAUNCH_PER_PASS, LAUNCH_PERSISTENT = 0, 1, 2
+LAUNCHES = {"auto": LAUNCH_AUTO, "per_pass": LAUNCH_PER_PASS, "persistent": LAUNCH_PERSISTENT}
 # single operators for qla_debug_apply: collisions (Eq. 17, Eq. 19), streaming
 # shifts S^{+-axis}_{components} (Eq. 18, Eq. 20), potentials (Eq. 21-22)
 OPS = {"CX": 0, "CX_T": 1, "CY": 2, "CY_T": 3, "S14+x": 4, "S14-x": 5, "S25+x": 6, "S25-x": 7,
@@ -37,7 +39,7 @@ EXPORTS = [
     "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
     "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc", "qla_sweep_split",
-    "qla_get_sweep_split",
+    "qla_get_sweep_split", "qla_sweep_dependencies", "qla_get_launch",
     "qla_batch_create", "qla_batch_run", "qla_batch_get_fields_f32", "qla_batch_diagnostics", "qla_batch_info",
     "qla_batch_set_wait_limit", "qla_batch_last_error", "qla_batch_destroy",
 ]
@@ -52,7 +54,7 @@ class QLAError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("sequence", ctypes.c_int), ("potential", ctypes.c_int),
                 ("steps_per_pass", ctypes.c_int), ("chunk_rows", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("families", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("families", ctypes.c_int), ("launch", ctypes.c_int)]
 
 
 class BufferSizes(ctypes.Structure):
@@ -131,6 +133,10 @@ def load_library(path: str = LIB_PATH):
     L.qla_sweep_split.restype = st
     L.qla_get_sweep_split.argtypes = [v, i, i, P(i), P(ctypes.c_longlong), i]
     L.qla_get_sweep_split.restype = st
+    L.qla_sweep_dependencies.argtypes = [i, i, i, i, i, i, P(i), i, P(i)]
+    L.qla_sweep_dependencies.restype = st
+    L.qla_get_launch.argtypes = [v, P(i)]
+    L.qla_get_launch.restype = st
     _lib = L
     return L
 
@@ -148,6 +154,22 @@ def sweep_split(Nx: int, Ny: int, steps_per_pass: int, ctas: int, precision: str
     if st != 0:
         raise QLAError(st, "qla_sweep_split")
     return out
+
+
+def sweep_dependencies(Nx: int, Ny: int, steps_per_pass: int, ctas: int, share: int,
+                       family: str = "TM") -> np.ndarray:
+    """Shares that share `share` of the persistent launch form waits for
+    before its passes after the first (host arithmetic of the library; no
+    GPU)."""
+    L = load_library()
+    out = np.zeros(int(ctas), dtype=np.int32)
+    n = ctypes.c_int()
+    st = L.qla_sweep_dependencies(int(Nx), int(Ny), int(steps_per_pass), int(ctas),
+                                  _code("family", {"TM": FAMILY_TM, "TE": FAMILY_TE}, family), int(share),
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), out.size, ctypes.byref(n))
+    if st != 0:
+        raise QLAError(st, "qla_sweep_dependencies")
+    return out[:n.value].copy()
 
 
 def _dptr(a: np.ndarray):
@@ -176,7 +198,7 @@ class Simulation:
 
     def __init__(self, n_x, n_y, n_z, delta: float, precision="fp32", sequence="interleaved",
                  potential="paper", steps_per_pass: int = 0, chunk_rows: int = 0,
-                 device: Optional[int] = None, stream=None, families="both"):
+                 device: Optional[int] = None, stream=None, families="both", launch="auto"):
         import torch  # device memory and streams
 
         if not torch.cuda.is_available():
@@ -207,6 +229,9 @@ class Simulation:
         # "TM": only (q2, q3, q4), the E_z polarisation; "TE": only (q0, q1, q5), E_y
         opt.families = _code("families", {"both": FAMILIES_BOTH, "TM": FAMILY_TM, "TE": FAMILY_TE}, families)
         self.families = families
+        # "per_pass": one kernel launch per pass; "persistent": the full passes
+        # of a step() call in one cooperative launch; "auto": one launch per pass
+        opt.launch = _code("launch", LAUNCHES, launch)
         self.precision = opt.precision
         sizes = BufferSizes()
         self._check(L.qla_query_buffer_sizes(self.Nx, self.Ny, ctypes.byref(opt), ctypes.byref(sizes)),
@@ -234,6 +259,13 @@ class Simulation:
         k, ch, pr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         L.qla_get_config(ctx, ctypes.byref(k), ctypes.byref(ch), ctypes.byref(pr))
         self.steps_per_pass, self.chunk_rows = k.value, ch.value
+
+    @property
+    def launch(self) -> str:
+        """The launch form the context's passes take: 'persistent' or 'per_pass'."""
+        v = ctypes.c_int()
+        self._check(self._L.qla_get_launch(self._ctx, ctypes.byref(v)), "qla_get_launch")
+        return "persistent" if v.value == LAUNCH_PERSISTENT else "per_pass"
 
     # -- plumbing ---------------------------------------------------------
     def _check(self, status: int, where: str):
