@@ -387,6 +387,8 @@ def run_ours(args):
     }
     if not args.skip_extras:
         line["single_family"] = single_family_report(w, args, peak, peak_kind)
+        # the other polarisation: the same lattice and pulse, E_y instead of E_z
+        line["single_family_other"] = single_family_report(w, args, peak, peak_kind, other=True)
         line["batch"] = batch_report(args, peak, peak_kind)
     if not args.skip_extras and not args.skip_surrogate:
         line["surrogate"] = surrogate_report()
@@ -395,19 +397,20 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def single_family_report(w, args, peak, peak_kind, steps: int = 5):
+def single_family_report(w, args, peak, peak_kind, steps: int = 5, other: bool = False):
     """The same workload with only the pulse's polarisation family stored and
     advanced (qla_options.families): the other family's three components are
     zero at the start and stay exactly zero under every operator, so the result
     is the same state (bit for bit, tested) for half the work. Its algorithmic
     bytes per site-update are those of the family's kernel (TM: 24 B of state +
-    4 B of n_z; TE: 24 B + 8 B of n_x, n_y)."""
+    4 B of n_z; TE: 24 B + 8 B of n_x, n_y). other: the pulse of the other
+    polarisation (same position, width and amplitude) and its family."""
     import torch
 
     from paper_2301_13601_gb300 import media
     from paper_2301_13601_gb300.qla import Simulation
 
-    fam, pol = ("TM", "Ez") if w.pulse.pol == media.POL_EZ else ("TE", "Ey")
+    fam, pol = ("TM", "Ez") if (w.pulse.pol == media.POL_EZ) != other else ("TE", "Ey")
     alg = 28.0 if fam == "TM" else 32.0
     S = QLA_STEPS_PER_BENCH_STEP
     with Simulation(*w.medium(), w.delta, precision="fp32", steps_per_pass=args.steps_per_pass,
