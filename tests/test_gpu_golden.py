@@ -10,9 +10,13 @@ Tolerances (targets: FP32 relative L2 <= 1e-4 after 1e4 steps, energy within
   * FP32 relative L2 <= 1e-4 (met with margin: 1.1e-5).
   * FP32 |E_gpu - E_oracle| / E(0) <= 2.5e-6 with the printed potentials: the
     measured 2.07e-6 with a 20% margin, so that a regression shows; the 1e-6
-    target is not met. The FP32 state rounding is amplified where the printed,
-    non-unitary potentials make the energy grow (+6.6% over this run); the same
-    rounding stays below 1e-6 when every operator is orthogonal
+    target is not met. The difference is systematic, not noise
+    (test_fp32_energy_difference_is_systematic): where the index field's
+    edges have thinned the potential angle below about 2^-24, a potential
+    row's increment is below half an ulp of its FP32 target and rounds away
+    at every application, so the FP32 run misses a few 1e-5 of the energy
+    the printed potentials inject (+6.6% over this run). With every operator
+    orthogonal the FP32 drift stays below 1e-6
     (test_unitary_fp32_energy_drift_full_length).
   * FP64 relative L2 <= 2e-11 at 1e4 steps: the oracle evaluates cos and sin
     of each angle in double and rounds them separately, so each of its
@@ -123,3 +127,45 @@ def test_fp64_vacuum_energy_is_conserved_where_the_oracle_drifts():
     assert abs(drift_oracle / (12 * d * T) - 1) < 0.02
     assert abs(drift_gpu) < 0.05 * abs(drift_oracle)
     assert abs(rel_l2(got, ref) / abs(drift_oracle / 2) - 1) < 0.1
+
+
+def test_fp32_energy_difference_is_systematic(golden):
+    """What the FP32 energy difference to the oracle is made of. The same run
+    from the oracle's initial state perturbed by one part in 1e7 per value
+    (about one FP32 ulp; the exact energy moves by ~1e-10 of E(0)) rounds
+    differently at every operator, so a random walk of rounding errors would
+    scatter the eight differences around zero. Measured on GB300 they agree
+    to 0.5% (-3.05e-6 +- 0.016e-6 of E(0) at step 10000; -4.8e-7 at 7500,
+    below 1e-7 up to 5000): the difference is a systematic property of the
+    FP32 evaluation of this workload, not noise, and it moves by 1e-6 between
+    this start and the device-initialised pulse of
+    test_ellipse_2048_fp32_full_length (2.07e-6 at most there). Guarded here:
+    the reproducibility, and a bound 15% above the measured value."""
+    import oracle
+
+    w = media.workload_ellipse_2048()
+    n = w.medium()
+    q0 = oracle.init_pulse(w.Nx, w.Ny, oracle.POL_EY, w.pulse.x0, w.pulse.sigma, w.pulse.amp)
+    steps = golden["steps"]
+    checks = [2500, 5000, 7500, 10000]
+    idx = [int(np.searchsorted(steps, s)) for s in checks]
+    E0 = golden["energy"][0]
+    rng = np.random.default_rng(11)
+    d = []
+    with Simulation(*n, w.delta, precision="fp32") as sim:
+        for k in range(8):
+            sim.set_fields(q0 * (1.0 + 1e-7 * rng.standard_normal(q0.shape)))
+            row, t = [], 0
+            for s, i in zip(checks, idx):
+                sim.step(s - t)
+                t = s
+                row.append((sim.diagnostics()["energy"] - golden["energy"][i]) / E0)
+            d.append(row)
+    d = np.array(d)
+    mean, sd = d.mean(axis=0), d.std(axis=0, ddof=1)
+    print("fp32 energy difference / E(0) at steps", checks)
+    for r in d:
+        print("  " + " ".join(f"{v:+.3e}" for v in r))
+    print("  mean " + " ".join(f"{v:+.3e}" for v in mean) + "\n  sd   " + " ".join(f"{v:.3e}" for v in sd))
+    assert sd[-1] <= 0.02 * abs(mean[-1]) + 2e-8
+    assert np.abs(d).max() <= 3.5e-6
