@@ -6,10 +6,9 @@
 // then for the next launch to start. Here CTA b keeps share b of each
 // advanced family for all the passes of the launch, one family after the
 // other. Before pass p >= 1 of a family it waits only for the shares of that
-// family whose pass p - 1 wrote
-// cells that share b reads, or read cells that share b overwrites: its halo
-// neighbours along its strip and in the strips beside it
-// (SweepSplit::shares_touch). Each CTA publishes its progress in a per-share
+// family whose pass p - 1 wrote cells that share b reads, or read cells that
+// share b overwrites: its halo neighbours along its strip and in the strips
+// beside it (SweepSplit::shares_touch). Each CTA publishes its progress in a per-share
 // pass counter (release store at GPU scope after its pass; the waiting CTA
 // reads it with acquire loads). A cooperative launch guarantees that all CTAs
 // (one per resident slot) run at once, so every wait ends; each is also bounded
