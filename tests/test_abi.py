@@ -80,6 +80,12 @@ def test_create_rejects_bad_arguments_before_touching_a_gpu(lib):
     assert L.qla_create(4, 4, P(nan), P(n), P(n), 0.1, None, None, ctypes.byref(ctx)) == 1
     assert L.qla_create(4, 4, P(n), P(n), P(n), 0.0, None, None, ctypes.byref(ctx)) == 1
     assert L.qla_create(4, 4, P(n), P(n), P(n), 0.7, None, None, ctypes.byref(ctx)) == 1
+    opt = qla.Options()
+    L.qla_default_options(ctypes.byref(opt))
+    assert opt.launch == qla.LAUNCH_AUTO
+    for bad_launch in (-1, 3):  # launch forms: automatic, one launch per pass, persistent
+        opt.launch = bad_launch
+        assert L.qla_create(4, 4, P(n), P(n), P(n), 0.1, ctypes.byref(opt), None, ctypes.byref(ctx)) == 1
     assert not ctx.value
 
 
