@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 # summary sits in profiles/ beside the launch list), valid while the sweep's code (comment lines
 # excluded), the workload, the steps per pass and the launch form (balanced split, one launch per
 # pass or all passes of a bench step in one persistent launch) match.
-MEASURED_TRAFFIC = {"sweep_sha256_prefix": "9a10d0e8a3b19081", "workload": "cylinders8192_fp32",
+MEASURED_TRAFFIC = {"sweep_sha256_prefix": "677c90822e6ffdd2", "workload": "cylinders8192_fp32",
                     "steps_per_pass": 2, "chunk_rows": 0, "launch": "per_pass", "bytes_per_launch": 7.77284e9}
 
 L2_BYTES = 129e6  # GB300 L2
@@ -115,13 +115,13 @@ class ClockSampler:
 
 
 def sweep_code_hash() -> str:
-    """sha256 prefix of the sweep kernel's sources (the kernel, its
+    """sha256 prefix of the per-pass sweep kernel's sources (the kernel, its
     instantiations and launch split, the shared declarations) with their
     comment lines removed."""
     import hashlib
 
     code = []
-    for name in ("qla_sweep.cuh", "qla_sweep_f32.cu", "qla_sweep_persist.cu", "qla_internal.h"):
+    for name in ("qla_sweep.cuh", "qla_sweep_f32.cu", "qla_internal.h"):
         with open(os.path.join(ROOT, "paper_2301_13601_gb300", "csrc", name)) as f:
             code += [l for l in f.read().splitlines() if not l.lstrip().startswith("//")]
     return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]

@@ -273,6 +273,15 @@ qla_status qla_get_config(const qla_ctx *ctx, int *steps_per_pass, int *chunk_ro
  * cooperative launch). QLA_EINVAL on NULL. */
 qla_status qla_get_launch(const qla_ctx *ctx, int *launch);
 
+/* Test hook of the persistent launch form: the limit in nanoseconds of the
+ * waits of one pass for the shares it depends on (default 2 s), and a number
+ * of extra passes every such wait demands (0 normally; a positive value makes
+ * the first wait run out, which must end the call with QLA_ETIMEOUT at the
+ * next synchronisation instead of hanging; the context then stays in that
+ * error). Takes effect at the next qla_step. QLA_EINVAL on NULL, a limit
+ * <= 0 or a negative withhold. */
+qla_status qla_set_wait_limit(qla_ctx *ctx, long long timeout_ns, int withhold);
+
 /* The balanced split of one fused pass of steps_per_pass steps (the sweep of
  * Eq. 28 / Eq. 23 over the lattice, one CTA grid layer per family). The
  * lattice is cut into strips of 256 - 8K output columns (K = steps_per_pass;

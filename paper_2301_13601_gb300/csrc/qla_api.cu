@@ -12,6 +12,13 @@
 #include "../../include/qla.h"
 #include "qla_internal.h"
 
+namespace qla {
+// The persistent launch with the test hook of its waits (qla_sweep_persist.cu).
+cudaError_t launch_sweep_persistent_hooked_f32(int K, const SweepArgs &a, int nfam, int passes, unsigned base,
+                                               unsigned *done, unsigned withhold, unsigned long long wait_ns,
+                                               cudaStream_t st);
+}  // namespace qla
+
 struct qla_ctx {
     int Nx = 0, Ny = 0;
     double delta = 0.0;
@@ -37,6 +44,8 @@ struct qla_ctx {
     bool persistent = false;        // passes of K steps in one cooperative launch per qla_step (QLA_LAUNCH_*)
     unsigned *pass_done = nullptr;  // device [2][kPersistMaxCtas]: passes completed per share (persistent form)
     unsigned pass_epoch = 0;        // passes the persistent launches have completed (the counters' base)
+    long long wait_ns = 2000000000LL;  // limit of a persistent pass's waits for its neighbours
+    unsigned withhold = 0;             // test hook: extra passes every such wait demands
     long long steps = 0;
     bool has_state = false;
     qla_status sticky = QLA_OK;
@@ -189,8 +198,9 @@ qla_status launch_persistent(qla_ctx *c, int passes, bool *refused) {
     const int nfam = c->opt.families == QLA_FAMILIES_BOTH ? 2 : 1;
     a.fam0 = c->opt.families == QLA_FAMILY_TE ? 1 : 0;
     a.error = c->sweep_err;
-    const cudaError_t e =
-        qla::launch_sweep_persistent_f32(K, a, nfam, passes, c->pass_epoch, c->pass_done, c->stream);
+    const cudaError_t e = qla::launch_sweep_persistent_hooked_f32(K, a, nfam, passes, c->pass_epoch, c->pass_done,
+                                                                  c->withhold, (unsigned long long)c->wait_ns,
+                                                                  c->stream);
     if (e == cudaErrorNotSupported || e == cudaErrorCooperativeLaunchTooLarge) {
         cudaGetLastError();
         *refused = true;
@@ -640,6 +650,13 @@ qla_status qla_sweep_dependencies(int Nx, int Ny, int steps_per_pass, int ctas, 
         deps[n++] = d;
     }
     *count = n;
+    return QLA_OK;
+}
+
+qla_status qla_set_wait_limit(qla_ctx *c, long long timeout_ns, int withhold) {
+    if (!c || timeout_ns <= 0 || withhold < 0) return QLA_EINVAL;
+    c->wait_ns = timeout_ns;
+    c->withhold = unsigned(withhold);
     return QLA_OK;
 }
 

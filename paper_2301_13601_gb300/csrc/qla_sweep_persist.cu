@@ -28,6 +28,8 @@ struct SweepPersistParams {
     int nfam;          // family layers advanced: the CTA sweeps share blockIdx.x of each
     unsigned base;     // pass counters reached by the earlier launches on these counters
     unsigned *done;    // [nfam][gridDim.x] passes each share has completed (monotonic across launches)
+    unsigned withhold;           // test hook: extra passes every wait demands (0 normally)
+    unsigned long long wait_ns;  // limit of one pass's waits
 };
 
 // A CTA's dependency lists, after the sweep's shared memory: per family up to
@@ -35,7 +37,7 @@ struct SweepPersistParams {
 // for every share of the family).
 constexpr int kPersistDeps = 64;
 constexpr size_t kPersistSmemExtra = 2 * kPersistDeps * sizeof(unsigned short) + 2 * sizeof(int);
-constexpr unsigned long long kPersistWaitNs = 2000000000ull;
+constexpr unsigned long long kPersistWaitNs = 2000000000ull;  // default wait limit
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, NY>::MINB)
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
             if (p > 0) {
                 // thread t waits for dependency t (t, t + NT, ... of all the
                 // family's shares when the list overflowed)
-                const unsigned target = pp.base + unsigned(p);
+                const unsigned target = pp.base + unsigned(p) + pp.withhold;
                 const int n = ndeps[f];
                 const bool all = n > kPersistDeps;
                 int stop = 0;
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
                             stop = 1;
                             break;
                         }
-                        if (global_ns() - t0 > kPersistWaitNs) {
+                        if (global_ns() - t0 > pp.wait_ns) {
                             atomicExch(prm.a.error, 1);
                             stop = 1;
                             break;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(SweepCfg<T, K, R, NY>::NT, SweepCfg<T, K, R, N
 
 template <typename T, int K, int R, int NY, bool INTER, bool UNIT>
 cudaError_t launch_persistent_t(const SweepArgs &a, int nfam, int passes, unsigned base, unsigned *done,
-                                cudaStream_t st) {
+                                unsigned withhold, unsigned long long wait_ns, cudaStream_t st) {
     using Cfg = SweepCfg<T, K, R, NY>;
     using L = SweepLayout<T, K, R, INTER>;
     auto kern = sweep_persistent_kernel<T, K, R, NY, INTER, UNIT>;
@@ -166,6 +168,8 @@ cudaError_t launch_persistent_t(const SweepArgs &a, int nfam, int passes, unsign
     pp.nfam = nfam;
     pp.base = base;
     pp.done = done;
+    pp.withhold = withhold;
+    pp.wait_ns = wait_ns;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(a.ctas), 1, 1);
     cfg.blockDim = dim3(unsigned(Cfg::NT), 1, 1);
@@ -179,15 +183,26 @@ cudaError_t launch_persistent_t(const SweepArgs &a, int nfam, int passes, unsign
     return cudaLaunchKernelEx(&cfg, kern, pp);
 }
 
-cudaError_t launch_sweep_persistent_f32(int K, const SweepArgs &a, int nfam, int passes, unsigned base,
-                                        unsigned *done, cudaStream_t st) {
+// The launch with its waits' test hook (qla_set_wait_limit): withhold extra
+// passes demanded by every wait, each pass's waits limited to wait_ns.
+cudaError_t launch_sweep_persistent_hooked_f32(int K, const SweepArgs &a, int nfam, int passes, unsigned base,
+                                               unsigned *done, unsigned withhold, unsigned long long wait_ns,
+                                               cudaStream_t st) {
     if (K != 2) return cudaErrorNotSupported;
     if (a.interleaved) {
-        return a.unitary ? launch_persistent_t<float, 2, 4, 2, true, true>(a, nfam, passes, base, done, st)
-                         : launch_persistent_t<float, 2, 4, 2, true, false>(a, nfam, passes, base, done, st);
+        return a.unitary
+                   ? launch_persistent_t<float, 2, 4, 2, true, true>(a, nfam, passes, base, done, withhold, wait_ns, st)
+                   : launch_persistent_t<float, 2, 4, 2, true, false>(a, nfam, passes, base, done, withhold, wait_ns,
+                                                                      st);
     }
-    return a.unitary ? launch_persistent_t<float, 2, 4, 2, false, true>(a, nfam, passes, base, done, st)
-                     : launch_persistent_t<float, 2, 4, 2, false, false>(a, nfam, passes, base, done, st);
+    return a.unitary
+               ? launch_persistent_t<float, 2, 4, 2, false, true>(a, nfam, passes, base, done, withhold, wait_ns, st)
+               : launch_persistent_t<float, 2, 4, 2, false, false>(a, nfam, passes, base, done, withhold, wait_ns, st);
+}
+
+cudaError_t launch_sweep_persistent_f32(int K, const SweepArgs &a, int nfam, int passes, unsigned base,
+                                        unsigned *done, cudaStream_t st) {
+    return launch_sweep_persistent_hooked_f32(K, a, nfam, passes, base, done, 0u, kPersistWaitNs, st);
 }
 
 bool sweep_persistent_supported(int precision, int K) { return precision == 0 && K == 2; }

@@ -39,7 +39,7 @@ EXPORTS = [
     "qla_get_fields",
     "qla_get_fields_f32", "qla_state_device_ptr", "qla_synchronize", "qla_step_count", "qla_get_config",
     "qla_last_error", "qla_status_string", "qla_destroy", "qla_diagnostics_noalloc", "qla_sweep_split",
-    "qla_get_sweep_split", "qla_sweep_dependencies", "qla_get_launch",
+    "qla_get_sweep_split", "qla_sweep_dependencies", "qla_get_launch", "qla_set_wait_limit",
     "qla_batch_create", "qla_batch_run", "qla_batch_get_fields_f32", "qla_batch_diagnostics", "qla_batch_info",
     "qla_batch_set_wait_limit", "qla_batch_last_error", "qla_batch_destroy",
 ]
@@ -137,6 +137,8 @@ def load_library(path: str = LIB_PATH):
     L.qla_sweep_dependencies.restype = st
     L.qla_get_launch.argtypes = [v, P(i)]
     L.qla_get_launch.restype = st
+    L.qla_set_wait_limit.argtypes = [v, ctypes.c_longlong, i]
+    L.qla_set_wait_limit.restype = st
     _lib = L
     return L
 
@@ -259,6 +261,10 @@ class Simulation:
         k, ch, pr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         L.qla_get_config(ctx, ctypes.byref(k), ctypes.byref(ch), ctypes.byref(pr))
         self.steps_per_pass, self.chunk_rows = k.value, ch.value
+
+    def set_wait_limit(self, timeout_ns: int, withhold: int = 0):
+        """Test hook of the persistent form's waits (qla_set_wait_limit)."""
+        self._check(self._L.qla_set_wait_limit(self._ctx, int(timeout_ns), int(withhold)), "qla_set_wait_limit")
 
     @property
     def launch(self) -> str:

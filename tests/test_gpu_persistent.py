@@ -10,6 +10,8 @@ strips, a ragged last strip, both families, one family, both step orders and
 potential variants, step counts with a shorter tail pass, several calls in a
 row with diagnostics between them; once against the FP64 oracle.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -102,3 +104,28 @@ def test_persistent_matches_oracle():
     q = oracle.init_pulse(Nx, Ny, oracle.POL_EY, 150.0, 25.0, 0.9)
     oracle.run(q, theta, beta, steps, oracle.SEQ_INTERLEAVED, oracle.POT_PAPER)
     assert np.linalg.norm(got - q) <= 3e-6 * np.linalg.norm(q)
+
+
+def test_persistent_wait_times_out_instead_of_hanging():
+    """Every wait of a persistent pass for its neighbours is bounded: with the
+    test hook demanding one pass more than any share will publish, the first
+    waits run out after 50 ms, every CTA stops, and the call's
+    synchronisation reports QLA_ETIMEOUT instead of hanging. The device stays
+    usable: a fresh context then agrees with one launch per pass."""
+    from paper_2301_13601_gb300.qla import QLAError
+
+    Nx, Ny = 1024, 512
+    n = media.smooth_periodic_medium(Nx, Ny, seed=3, amp=0.3)
+    with Simulation(*n, 0.1, launch="persistent") as sim:
+        assert sim.launch == "persistent"
+        sim.set_fields(fields(Nx, Ny, 1))
+        sim.set_wait_limit(50_000_000, withhold=1)  # a pass that never comes
+        t0 = time.time()
+        sim.step(10)
+        with pytest.raises(QLAError) as err:
+            sim.synchronize()
+        assert err.value.status == 4  # QLA_ETIMEOUT
+        assert time.time() - t0 < 30.0
+    _, got, _ = run(512, 200, "persistent", (6,))
+    _, ref, _ = run(512, 200, "per_pass", (6,))
+    assert np.array_equal(got, ref)
