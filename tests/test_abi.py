@@ -87,6 +87,10 @@ def test_create_rejects_bad_arguments_before_touching_a_gpu(lib):
         opt.launch = bad_launch
         assert L.qla_create(4, 4, P(n), P(n), P(n), 0.1, ctypes.byref(opt), None, ctypes.byref(ctx)) == 1
     assert not ctx.value
+    # the persistent form's wait hook and launch query reject a missing context
+    assert L.qla_set_wait_limit(None, 1000, 0) == 1
+    launch = ctypes.c_int()
+    assert L.qla_get_launch(None, ctypes.byref(launch)) == 1
 
 
 def test_conv_rejects_bad_arguments_without_gpu(lib):
